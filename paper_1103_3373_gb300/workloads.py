@@ -1,0 +1,160 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Sec. 5).
+
+This module only builds initial conditions and work lists; it holds no step
+of the solver.  Both the CUDA path's tests/benchmarks and the CPU oracle take
+their inputs from here.  Fields are numpy float64 arrays [5, Z, Y, X] of the
+conserved variables (rho, rho u, rho v, rho w, E) of an ideal gas, built from
+primitive initial data with E = p / (gamma - 1) + rho |v|^2 / 2 (the
+definition of the initial state, not part of the update).
+
+Workloads (Sec. 5 of the paper uses a 3D blast wave and a cosmological AMR
+run; their data are not available, so these stand in for them):
+  * sod(n, axis)             Sod shock tube, rho/p = 1/1 | 0.125/0.1
+  * lognormal(n, seed, ...)  periodic lognormal density (sigma 0.5, k^-3
+                             Gaussian field), p = 1, random k^-3 velocities
+                             scaled to an rms Mach number
+  * sedov(n)                 Sedov-Taylor blast: E = 1 in r < 2 cells
+  * sound_wave / advection / uniform: small analytic cases for the pins
+"""
+import numpy as np
+
+
+def conserved(rho, vx, vy, vz, p, gamma):
+    """Initial conserved state [5, ...] from primitive initial data."""
+    rho = np.asarray(rho, dtype=np.float64)
+    shape = rho.shape
+    vx, vy, vz, p = (np.broadcast_to(np.asarray(a, dtype=np.float64), shape) for a in (vx, vy, vz, p))
+    U = np.empty((5,) + shape)
+    U[0] = rho
+    U[1] = rho * vx
+    U[2] = rho * vy
+    U[3] = rho * vz
+    U[4] = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz)
+    return U
+
+
+def cell_centres(n, length=1.0):
+    dx = length / n
+    x = (np.arange(n) + 0.5) * dx
+    return x, dx
+
+
+def uniform(shape, rho=1.0, v=(0.3, -0.2, 0.1), p=0.7, gamma=1.4):
+    r = np.full(shape, rho)
+    return conserved(r, v[0], v[1], v[2], p, gamma)
+
+
+def sod(n, axis=0, gamma=1.4, ny=None, nz=None, diagonal=False):
+    """Sod tube on [0,1]^3 (interface x_axis = 0.5, or x+y+z = 1.5 if diagonal)."""
+    nx = n
+    ny = ny or n
+    nz = nz or n
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    z = (np.arange(nz) + 0.5) / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    coord = (X, Y, Z)[axis]
+    left = (X + Y + Z < 1.5) if diagonal else (coord < 0.5)
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    return conserved(rho, 0.0, 0.0, 0.0, p, gamma)
+
+
+def gaussian_field(n, seed, slope=-3.0):
+    """Unit-variance periodic Gaussian random field with P(k) ~ k^slope on n^3."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal((n, n, n))
+    k = np.fft.fftfreq(n) * n
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(kk)
+    nz = kk > 0
+    amp[nz] = kk[nz] ** (slope / 2.0)
+    f = np.fft.ifftn(np.fft.fftn(white) * amp).real
+    f -= f.mean()
+    f /= f.std()
+    return f
+
+
+def lognormal(n, seed=1, sigma=0.5, mach=1.5, gamma=1.4, p0=1.0, vel_seeds=None):
+    """Periodic lognormal box: rho = exp(sigma d - sigma^2/2), p = p0, and three
+    independent k^-3 velocity components scaled so that sqrt(<|v|^2/c^2>) = mach."""
+    d = gaussian_field(n, seed)
+    rho = np.exp(sigma * d - 0.5 * sigma * sigma)
+    vs = vel_seeds or (seed + 1, seed + 2, seed + 3)
+    v = [gaussian_field(n, s) for s in vs]
+    c2 = gamma * p0 / rho
+    m2 = (v[0] ** 2 + v[1] ** 2 + v[2] ** 2) / c2
+    scale = mach / np.sqrt(m2.mean())
+    return conserved(rho, scale * v[0], scale * v[1], scale * v[2], p0, gamma)
+
+
+def sedov(n, gamma=5.0 / 3.0, E=1.0, rho0=1.0, p0=1.0e-5, r_cells=2.0):
+    """Sedov-Taylor blast on [0,1]^3: E spread uniformly over the cells whose
+    centre lies within r_cells cell widths of the box centre."""
+    x, dx = cell_centres(n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    inside = r < r_cells * dx
+    U = conserved(np.full((n, n, n), rho0), 0.0, 0.0, 0.0, p0, gamma)
+    U[4][inside] += E / (inside.sum() * dx ** 3)
+    return U
+
+
+def sound_wave(n, amp=1.0e-6, gamma=1.4, direction=(1, 0, 0), shape=None):
+    """Right-moving linear sound wave, rho0 = 1, c = 1 (p0 = 1/gamma), wave
+    vector 2 pi direction on the periodic unit box."""
+    shape = shape or (n, n, n)
+    nz, ny, nx = shape
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    z = (np.arange(nz) + 0.5) / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    kd = np.asarray(direction, dtype=np.float64)
+    phase = 2 * np.pi * (kd[0] * X + kd[1] * Y + kd[2] * Z)
+    nhat = kd / np.linalg.norm(kd)
+    s = amp * np.sin(phase)
+    return conserved(1.0 + s, nhat[0] * s, nhat[1] * s, nhat[2] * s, 1.0 / gamma + s, gamma)
+
+
+def advection(shape, velocity=(1.0, 0.0, 0.0), gamma=1.4, kind="sine", axis=0):
+    """Density profile carried by a uniform velocity at uniform pressure."""
+    nz, ny, nx = shape
+    n_ax = (nx, ny, nz)[axis]
+    s = (np.arange(n_ax) + 0.5) / n_ax
+    if kind == "sine":
+        prof = 1.0 + 0.5 * np.sin(2 * np.pi * s)
+    else:  # square pulse
+        prof = np.where((s > 0.25) & (s < 0.5), 2.0, 1.0)
+    sh = [1, 1, 1]
+    sh[2 - axis] = n_ax
+    rho = np.broadcast_to(prof.reshape(sh), shape).copy()
+    return conserved(rho, velocity[0], velocity[1], velocity[2], 1.0, gamma)
+
+
+def group_origins(X, Y, Z, N=16):
+    """Interior corners (x0, y0, z0) of the N^3 groups tiling an X x Y x Z box,
+    group index (gz * GY + gy) * GX + gx."""
+    assert X % N == 0 and Y % N == 0 and Z % N == 0
+    o = [(gx * N, gy * N, gz * N) for gz in range(Z // N) for gy in range(Y // N) for gx in range(X // N)]
+    return np.asarray(o, dtype=np.int32).reshape(-1, 3)
+
+
+def scatter_groups(U_groups, X, Y, Z):
+    """Inverse of the interior tiling: [G,5,N,N,N] -> [5,Z,Y,X]."""
+    G, _, N = U_groups.shape[:3]
+    GX, GY, GZ = X // N, Y // N, Z // N
+    a = U_groups.reshape(GZ, GY, GX, 5, N, N, N)
+    return a.transpose(3, 0, 4, 1, 5, 2, 6).reshape(5, Z, Y, X)
+
+
+def poisson_arrivals(rate=200.0, n=2000, seed=6):
+    """Serving requests: arrival time, box size, rms Mach, step count, seed."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    sizes = rng.choice([32, 64, 128, 256], size=n, p=[0.4, 0.3, 0.2, 0.1])
+    mach = rng.uniform(0.5, 3.0, n)
+    steps = rng.integers(5, 51, n)
+    seeds = rng.integers(0, 2 ** 31 - 1, n)
+    return [dict(t=float(t[i]), n=int(sizes[i]), mach=float(mach[i]), steps=int(steps[i]), seed=int(seeds[i]))
+            for i in range(n)]

@@ -1,0 +1,357 @@
+"""Pins of the oracle's building blocks against facts fixed outside the oracle.
+
+Limiters (Sec. 2; Toro 2009): consistency phi(1) = 1, odd symmetry, the TVD
+bound |delta| <= 2 min(|dL|, |dR|), hand-evaluated values.
+Reconstruction (Sec. 2): exactness on linear data, no new extrema.
+CTU tracing (Sec. 2 step (1)): closed forms in terms of the primitive Jacobian
+for fully upwind cases, exact transport of a single characteristic wave.
+Riemann solvers (Sec. 2): Toro's exact star states, Rankine-Hugoniot and
+isentropic relations, consistency, mirror symmetry, contact preservation,
+Roe's exactness on a single shock, HLLE positivity and Roe's failure on the
+strong double rarefaction that triggers the fallback.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LIMITERS = [O.MINMOD, O.VANLEER, O.VANALBADA, O.HYBRID]
+SOLVERS = [O.EXACT, O.HLLE, O.HLLC, O.ROE]
+
+
+# ----------------------------------------------------------------- limiters
+@pytest.mark.parametrize("lim", LIMITERS)
+@pytest.mark.parametrize("theta", [1.0, 1.5, 2.0])
+def test_limiter_invariants(lim, theta):
+    rng = np.random.default_rng(10 + lim)
+    for _ in range(300):
+        a, b = rng.normal(size=2) * 10.0 ** rng.uniform(-3, 2, size=2)
+        d = O.limiter(lim, a, b, theta)
+        # phi(1) = 1: equal differences are reproduced
+        assert O.limiter(lim, a, a, theta) == pytest.approx(a, rel=1e-15)
+        # zero at extrema, symmetric in its arguments, odd
+        if a * b <= 0:
+            assert d == 0.0
+        else:
+            assert np.sign(d) == np.sign(a)
+            assert abs(d) <= 2 * min(abs(a), abs(b)) * (1 + 1e-15)  # TVD region
+        assert O.limiter(lim, b, a, theta) == pytest.approx(d, rel=1e-15, abs=0)
+        assert O.limiter(lim, -a, -b, theta) == pytest.approx(-d, rel=1e-15, abs=0)
+
+
+def test_limiter_hand_values():
+    # dL = 1, dR = 3 (dC = 2), evaluated by hand from the textbook definitions
+    assert O.limiter(O.MINMOD, 1, 3, 1.0) == 1.0          # classic minmod
+    assert O.limiter(O.MINMOD, 1, 3, 1.5) == 1.5
+    assert O.limiter(O.MINMOD, 1, 3, 2.0) == 2.0          # MC: min(2, 6, 2)
+    assert O.limiter(O.VANLEER, 1, 3) == 1.5              # harmonic mean 2*3/4
+    assert O.limiter(O.VANALBADA, 1, 3) == pytest.approx(1.2)  # 3*4/10
+    assert O.limiter(O.HYBRID, 1, 3, 1.2) == pytest.approx(1.2)  # theta*min bound
+    assert O.limiter(O.HYBRID, 1, 3, 2.0) == 1.5          # van Leer bound
+    assert O.limiter(O.MINMOD, -2, -5, 1.0) == -2.0
+    assert O.limiter(O.VANLEER, 2, 6) == 3.0
+
+
+def test_classic_minmod_reduction():
+    # generalized minmod with theta = 1 is the textbook minmod(a, b)
+    rng = np.random.default_rng(3)
+    for a, b in rng.normal(size=(200, 2)):
+        ref = 0.0 if a * b <= 0 else np.sign(a) * min(abs(a), abs(b))
+        assert O.limiter(O.MINMOD, a, b, 1.0) == ref
+
+
+# ------------------------------------------------------------ reconstruction
+@pytest.mark.parametrize("recon", [O.PLM, O.PPM])
+@pytest.mark.parametrize("lim", LIMITERS)
+def test_recon_exact_on_linear(recon, lim):
+    i = np.arange(12, dtype=np.float64)
+    w = 0.7 - 0.3 * i
+    wL, wR = O.recon1d(recon, lim, w, theta=1.5)
+    s = 2 if recon == O.PPM else 1
+    sl = slice(s, 12 - s)
+    np.testing.assert_allclose(wL[sl], 0.7 - 0.3 * (i[sl] - 0.5), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(wR[sl], 0.7 - 0.3 * (i[sl] + 0.5), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("recon", [O.PLM, O.PPM])
+@pytest.mark.parametrize("lim", LIMITERS)
+def test_recon_no_new_extrema(recon, lim):
+    rng = np.random.default_rng(7)
+    w = np.cumsum(rng.normal(size=200)) + 5 * np.sign(np.sin(np.arange(200) / 9.0))
+    wL, wR = O.recon1d(recon, lim, w, theta=2.0)
+    s = 2 if recon == O.PPM else 1
+    for i in range(s, 200 - s):
+        lo = min(w[i - 1], w[i], w[i + 1]) - 1e-12
+        hi = max(w[i - 1], w[i], w[i + 1]) + 1e-12
+        assert lo <= wL[i] <= hi and lo <= wR[i] <= hi
+        if recon == O.PPM:
+            # CW84: after the constraints the parabola has no interior extremum
+            dA = wR[i] - wL[i]
+            a6 = 6 * (w[i] - 0.5 * (wL[i] + wR[i]))
+            assert abs(a6) <= abs(dA) * (1 + 1e-9) + 1e-12
+        if (w[i + 1] - w[i]) * (w[i] - w[i - 1]) <= 0:  # local extremum -> flat
+            assert wL[i] == w[i] and wR[i] == w[i]
+
+
+# ------------------------------------------------------------------ tracing
+def prim_jacobian(W, gamma):
+    """A(W) of W_t + A W_x = 0 for W = (rho, u, v, w, p), the Euler equations."""
+    rho, u, _, _, p = W
+    A = np.diag([u] * 5).astype(np.float64)
+    A[0, 1] = rho
+    A[1, 4] = 1.0 / rho
+    A[4, 1] = gamma * p
+    return A
+
+
+@pytest.mark.parametrize("u", [2.5, -2.5])
+def test_trace_plm_fully_upwind_closed_form(u):
+    g = 1.4
+    W0 = np.array([1.3, u, 0.2, -0.4, 1.1])  # c = 1.08 < |u|: all waves one-sided
+    dW = np.array([0.05, -0.02, 0.01, 0.03, -0.04])
+    dtdx = 0.3
+    Wl, Wr = O.trace(O.PLM, W0, dW, None, dtdx, g)
+    A = prim_jacobian(W0, g)
+    I = np.eye(5)
+    if u > 0:
+        np.testing.assert_allclose(Wr, W0 + 0.5 * (I - dtdx * A) @ dW, rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(Wl, W0 - 0.5 * dW, rtol=1e-14, atol=1e-15)
+    else:
+        np.testing.assert_allclose(Wl, W0 - 0.5 * (I + dtdx * A) @ dW, rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(Wr, W0 + 0.5 * dW, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("u", [2.5, -2.5])
+def test_trace_ppm_fully_upwind_closed_form(u):
+    g = 1.4
+    W0 = np.array([1.3, u, 0.2, -0.4, 1.1])
+    WL = W0 + np.array([-0.03, 0.01, -0.02, 0.02, 0.05])
+    WR = W0 + np.array([0.04, -0.02, 0.01, 0.01, -0.03])
+    dtdx = 0.25
+    Wl, Wr = O.trace(O.PPM, W0, WL, WR, dtdx, g)
+    A = prim_jacobian(W0, g)
+    dA = WR - WL
+    W6 = 6 * (W0 - 0.5 * (WL + WR))
+    if u > 0:
+        # average of the parabola over each wave's domain of dependence, all waves right-moving
+        ref = WR - 0.5 * dtdx * A @ (dA - W6) - dtdx ** 2 / 3.0 * A @ A @ W6
+        np.testing.assert_allclose(Wr, ref, rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(Wl, WL, rtol=1e-14, atol=1e-15)
+    else:
+        ref = WL - 0.5 * dtdx * A @ (dA + W6) - dtdx ** 2 / 3.0 * A @ A @ W6
+        np.testing.assert_allclose(Wl, ref, rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(Wr, WR, rtol=1e-14, atol=1e-15)
+
+
+def test_trace_single_wave_transport():
+    # slope along one right eigenvector (from numpy's eigen-decomposition of A):
+    # the traced right-edge state transports exactly that wave by its speed
+    g = 1.4
+    W0 = np.array([1.0, 0.3, 0.1, 0.2, 0.9])
+    A = prim_jacobian(W0, g)
+    lam, R = np.linalg.eig(A)
+    dtdx = 0.4
+    for k in range(5):
+        if lam[k].real <= 0:
+            continue
+        dW = 0.01 * R[:, k].real
+        Wl, Wr = O.trace(O.PLM, W0, dW, None, dtdx, g)
+        np.testing.assert_allclose(Wr, W0 + 0.5 * (1 - lam[k].real * dtdx) * dW, rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------------ Riemann
+def prim2cons(W, g):
+    r, u, v, w, p = W
+    return np.array([r, r * u, r * v, r * w, p / (g - 1) + 0.5 * r * (u * u + v * v + w * w)])
+
+
+def euler_flux_x(U, g):
+    """Physical flux along x of the Euler equations (definition)."""
+    r, mx, my, mz, E = U
+    u = mx / r
+    p = (g - 1) * (E - 0.5 * (mx * mx + my * my + mz * mz) / r)
+    return np.array([mx, mx * u + p, my * u, mz * u, (E + p) * u])
+
+
+def random_state(rng, g=1.4):
+    return prim2cons([rng.uniform(0.1, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.1, 2)], g)
+
+
+def load_toro():
+    rows = np.loadtxt(os.path.join(GOLDEN, "toro_exact_star.txt"))
+    return rows
+
+
+def test_exact_solver_toro_tables():
+    for row in load_toro():
+        WL = np.array([row[0], row[1], 0, 0, row[2]])
+        WR = np.array([row[3], row[4], 0, 0, row[5]])
+        ps, us, it, _ = O.exact_star(WL, WR)
+        assert it > 0
+        assert ps == pytest.approx(row[6], rel=2e-5, abs=1e-5)
+        assert us == pytest.approx(row[7], rel=2e-5, abs=1e-5)
+        # star densities: sample just left / right of the contact
+        _, _, _, Ws = O.exact_star(WL, WR, xi=[us - 1e-9, us + 1e-9])
+        # the table prints 5 decimals or 6 significant digits
+        assert Ws[0, 0] == pytest.approx(row[8], rel=2e-5, abs=6e-6)
+        assert Ws[1, 0] == pytest.approx(row[9], rel=2e-5, abs=6e-6)
+
+
+def shock_jump_residual(Wa, Wb, S, g):
+    """Rankine-Hugoniot residuals F(b) - F(a) - S (U(b) - U(a)) for a jump moving at S."""
+    Ua, Ub = prim2cons(Wa, g), prim2cons(Wb, g)
+    return euler_flux_x(Ub, g) - euler_flux_x(Ua, g) - S * (Ub - Ua)
+
+
+@pytest.mark.parametrize("row", range(5))
+def test_exact_solution_jump_conditions(row):
+    """Across each shock the sampled solution satisfies Rankine-Hugoniot; in
+    each fan the entropy p/rho^gamma and the Riemann invariant are constant."""
+    g = 1.4
+    r = load_toro()[row]
+    WL = np.array([r[0], r[1], 0.0, 0.0, r[2]])
+    WR = np.array([r[3], r[4], 0.0, 0.0, r[5]])
+    ps, us, it, _ = O.exact_star(WL, WR)
+    span = 40.0
+    xi = np.linspace(-span, span, 400001)
+    _, _, _, W = O.exact_star(WL, WR, xi=xi)
+    rho = W[:, 0]
+    jumps = np.nonzero(np.abs(np.diff(rho)) > 1e-6 * rho.max() * 50)[0]
+    # group consecutive indices into discontinuities and fans
+    for side, Wk in ((-1, WL), (1, WR)):
+        if ps > Wk[4]:  # shock on this side: find the jump adjacent to the far state
+            idx = np.nonzero(np.all(np.isclose(W, Wk, rtol=0, atol=1e-12), axis=1))[0]
+            k = idx.max() if side < 0 else idx.min()
+            a, b = (k, k + 1) if side < 0 else (k - 1, k)
+            # mass conservation fixes S; momentum and energy must then balance
+            Ua, Ub = prim2cons(W[a], g), prim2cons(W[b], g)
+            S = (euler_flux_x(Ub, g)[0] - euler_flux_x(Ua, g)[0]) / (Ub[0] - Ua[0])
+            res = shock_jump_residual(W[a], W[b], S, g)
+            scale = np.abs(euler_flux_x(Ua, g)).max() + np.abs(S * Ua).max()
+            assert np.abs(res).max() <= 1e-10 * scale
+        else:  # rarefaction: isentropic, with a constant Riemann invariant
+            c = np.sqrt(g * W[:, 4] / W[:, 0])
+            sgn = 1.0 if side < 0 else -1.0
+            sel = (xi < us) if side < 0 else (xi > us)
+            ent = W[sel, 4] / W[sel, 0] ** g
+            inv = W[sel, 1] + sgn * 2 * c[sel] / (g - 1)
+            assert np.ptp(ent) <= 1e-10 * ent.max()
+            assert np.ptp(inv) <= 1e-10 * np.abs(inv).max() + 1e-12
+    # pressure and normal velocity are continuous across the contact
+    _, _, _, Wc = O.exact_star(WL, WR, xi=[us - 1e-7, us + 1e-7])
+    assert Wc[0, 4] == pytest.approx(Wc[1, 4], rel=1e-12)
+    assert Wc[0, 1] == pytest.approx(Wc[1, 1], rel=1e-12)
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_riemann_consistency(solver):
+    rng = np.random.default_rng(20 + solver)
+    for _ in range(50):
+        U = random_state(rng)
+        F, st = O.riemann(solver, U, U, d=0)
+        np.testing.assert_allclose(F, euler_flux_x(U, 1.4), rtol=1e-13, atol=1e-14)
+        assert st == 0
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_riemann_mirror_symmetry(solver):
+    rng = np.random.default_rng(30 + solver)
+    flip = np.array([1, -1, 1, 1, 1.0])
+    sgn = np.array([-1, 1, -1, -1, -1.0])
+    for _ in range(50):
+        UL, UR = random_state(rng), random_state(rng)
+        F, _ = O.riemann(solver, UL, UR)
+        Fm, _ = O.riemann(solver, UR * flip, UL * flip)
+        np.testing.assert_allclose(Fm, sgn * F, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_riemann_direction_rotation(solver):
+    rng = np.random.default_rng(40 + solver)
+    for _ in range(20):
+        UL, UR = random_state(rng), random_state(rng)
+        Fx, _ = O.riemann(solver, UL, UR, d=0)
+        # the same local problem posed along y: (m_y, m_z, m_x) <- (m_x, m_y, m_z)
+        perm_y = lambda U: np.array([U[0], U[3], U[1], U[2], U[4]])
+        Fy, _ = O.riemann(solver, perm_y(UL), perm_y(UR), d=1)
+        np.testing.assert_array_equal(Fy, perm_y(Fx))
+        perm_z = lambda U: np.array([U[0], U[2], U[3], U[1], U[4]])
+        Fz, _ = O.riemann(solver, perm_z(UL), perm_z(UR), d=2)
+        np.testing.assert_array_equal(Fz, perm_z(Fx))
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_riemann_supersonic_upwind(solver):
+    g = 1.4
+    UL = prim2cons([1.0, 3.0, 0.2, 0.1, 0.8], g)
+    UR = prim2cons([0.6, 2.8, -0.1, 0.3, 0.5], g)
+    F, _ = O.riemann(solver, UL, UR)
+    np.testing.assert_allclose(F, euler_flux_x(UL, g), rtol=1e-13, atol=1e-14)
+    F, _ = O.riemann(solver, UR * [1, -1, 1, 1, 1], UL * [1, -1, 1, 1, 1])
+    np.testing.assert_allclose(F, euler_flux_x(UL * [1, -1, 1, 1, 1], g), rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_stationary_contact(solver):
+    g = 1.4
+    UL = prim2cons([1.0, 0.0, 0.3, -0.2, 0.7], g)
+    UR = prim2cons([0.2, 0.0, -0.5, 0.4, 0.7], g)
+    F, _ = O.riemann(solver, UL, UR)
+    if solver == O.HLLE:
+        assert abs(F[0]) > 1e-3  # HLLE smears contacts (Sec. 2)
+    else:
+        np.testing.assert_allclose(F, [0, 0.7, 0, 0, 0], atol=1e-14)
+
+
+def test_roe_exact_for_single_shock():
+    g = 1.4
+    for M in (1.5, 3.0, 8.0):
+        r1, p1, u1 = 0.8, 0.6, 0.1
+        c1 = np.sqrt(g * p1 / r1)
+        S = u1 + M * c1  # shock moving right into state 1
+        # normal-shock relations (textbook)
+        r2 = r1 * (g + 1) * M * M / ((g - 1) * M * M + 2)
+        p2 = p1 * (1 + 2 * g / (g + 1) * (M * M - 1))
+        u2 = S + r1 * (u1 - S) / r2
+        UL = prim2cons([r2, u2, 0.3, -0.1, p2], g)
+        UR = prim2cons([r1, u1, 0.3, -0.1, p1], g)
+        assert np.abs(shock_jump_residual([r2, u2, .3, -.1, p2], [r1, u1, .3, -.1, p1], S, g)).max() < 1e-11 * p2
+        F, ok = O.roe_only(UL, UR)
+        assert ok
+        np.testing.assert_allclose(F, euler_flux_x(UL, g), rtol=1e-12, atol=1e-12)
+
+
+def test_hlle_positive_and_roe_fallback_on_double_rarefaction():
+    g = 1.4
+    for u in (2.0, 3.0, 4.0):
+        UL = prim2cons([1.0, -u, 0.0, 0.0, 0.4], g)
+        UR = prim2cons([1.0, u, 0.0, 0.0, 0.4], g)
+        F, _ = O.riemann(O.HLLE, UL, UR)
+        # the HLL intermediate state behind the flux, U* = UL + (F - FL)/SL, is physical
+        ok_roe = O.roe_only(UL, UR)[1]
+        assert not ok_roe  # linearisation fails (Einfeldt 1991, Sec. 2)
+        Ffb, st = O.riemann(O.ROE, UL, UR, fallback=O.HLLE)
+        np.testing.assert_array_equal(Ffb, F)
+        assert st & O.ST_ROE_FALLBACK
+        cL = np.sqrt(g * 0.4)
+        SL = -u - cL
+        Us = UL + (F - euler_flux_x(UL, g)) / SL
+        pstar = (g - 1) * (Us[4] - 0.5 * Us[1] ** 2 / Us[0])
+        assert Us[0] > 0 and pstar > 0
+        for fb in (O.HLLC, O.EXACT):
+            Ffb2, st2 = O.riemann(O.ROE, UL, UR, fallback=fb)
+            Fref, _ = O.riemann(fb, UL, UR)
+            np.testing.assert_array_equal(Ffb2, Fref)
+            assert st2 & O.ST_ROE_FALLBACK
+
+
+def test_exact_vacuum_is_reported():
+    g = 1.4
+    UL = prim2cons([1.0, -20.0, 0, 0, 0.4], g)
+    UR = prim2cons([1.0, 20.0, 0, 0, 0.4], g)
+    F, st = O.riemann(O.EXACT, UL, UR)
+    assert st & O.ST_EXACT_FAIL
+    assert np.all(np.isfinite(F))
