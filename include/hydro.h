@@ -1,0 +1,219 @@
+/*
+ * libhydro — GB300 (sm_103a) directionally unsplit Riemann-solver fluid update
+ * of a batch of AMR patch groups (3D Euler equations of an ideal gas).
+ *
+ * Method: Schive, Zhang & Chiueh, "Directionally Unsplit Hydrodynamic Schemes
+ * with Hybrid MPI/OpenMP/GPU Parallelization in AMR" (arXiv:1103.3373).
+ *   Sec. 2      the MHM, VL and 6-solve CTU schemes; PLM/PPM reconstruction
+ *               with the generalized minmod, van Leer, van Albada and hybrid
+ *               limiters; exact, HLLE, HLLC and Roe solvers with the Roe
+ *               failure fallback; the five CTU steps (reconstruct + trace,
+ *               Riemann, transverse correction + Riemann, conservative
+ *               update, store the patch-boundary fluxes).
+ *   Sec. 3.1    one patch group = 2x2x2 patches of 8^3 cells (16^3 cells)
+ *               plus ghost zones, computed by one thread block; arrays
+ *               flattened as [z][y][x] with x fastest.
+ *   Sec. 4.1    solver input / output arrays are group-major, contiguous per
+ *               group ([groups][size per group]).
+ *   Sec. 4.2    the preparation step (ghost-zone gather) and Sec. 4.3 the
+ *               evolution time step, here device kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Conserved variables, in this order: rho, rho*u, rho*v, rho*w, E.
+ *   - A "group" holds N^3 interior cells (N = 16, or 8 for single patches).
+ *     Group input  U_in : [G][5][M][M][M], M = N + 2*ghost, x fastest.
+ *     Group output U_out: [G][5][N][N][N].
+ *     Boundary flux     : [G][6][5][N][N]; faces -x,+x,-y,+y,-z,+z; the two
+ *                         transverse indices in [z][y][x] order with the
+ *                         normal one removed; time-centred flux F (not dt*F),
+ *                         positive along +axis.
+ *     Uniform field     : [5][Z][Y][X].
+ *   - Storage precision: FP64 -> double; FP32 and FP32_MIXED -> float.
+ *   - All pointers named *_dev or documented as "device" are device memory
+ *     owned by the caller; the library never allocates, frees or keeps them.
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  No call synchronises the device,
+ *     except where stated.
+ *   - Return value: HYDRO_OK or a negative HYDRO_E* code for argument,
+ *     configuration or launch errors, detected synchronously.  Numerical
+ *     failures are reported asynchronously through the per-group status word.
+ *     The library never traps.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- enumerations (Sec. 2) ---------------------------------------------- */
+enum { HYDRO_MHM = 0, HYDRO_VL = 1, HYDRO_CTU = 2 };                 /* scheme   */
+enum { HYDRO_PLM = 0, HYDRO_PPM = 1 };                               /* recon    */
+enum { HYDRO_LIM_MINMOD = 0, HYDRO_LIM_VANLEER = 1,                  /* limiter  */
+       HYDRO_LIM_VANALBADA = 2, HYDRO_LIM_HYBRID = 3 };
+enum { HYDRO_RS_EXACT = 0, HYDRO_RS_HLLE = 1, HYDRO_RS_HLLC = 2,     /* Riemann  */
+       HYDRO_RS_ROE = 3 };
+enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_FP32_MIXED = 2 };       /* precision */
+enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge  */
+
+/* ---- return codes ----------------------------------------------------------- */
+#define HYDRO_OK 0
+#define HYDRO_EINVAL (-1)       /* bad argument (null pointer, size, enum)        */
+#define HYDRO_EGHOST (-2)       /* ghost width below what the scheme needs        */
+#define HYDRO_EUNSUPPORTED (-3) /* valid but not built (e.g. N other than 8, 16)  */
+#define HYDRO_ECUDA (-4)        /* a CUDA call failed (see hydro_last_cuda_error) */
+#define HYDRO_EWORKSPACE (-5)   /* workspace missing or smaller than required     */
+
+/* ---- per-group status bits (written, not OR-ed, once per group and call) --- */
+#define HYDRO_ST_ROE_FALLBACK 1u /* informational: Roe failed at >= 1 face and the
+                                    fallback solver was used there (Sec. 2)       */
+#define HYDRO_ST_NEG_DENS 2u     /* an updated density <= 0                      */
+#define HYDRO_ST_NEG_PRES 4u     /* an updated pressure <= 0                     */
+#define HYDRO_ST_NAN 8u          /* NaN in the updated state                     */
+#define HYDRO_ST_EXACT_FAIL 16u  /* exact solver: vacuum or no convergence       */
+#define HYDRO_ST_ERROR_MASK (HYDRO_ST_NEG_DENS | HYDRO_ST_NEG_PRES | HYDRO_ST_NAN | HYDRO_ST_EXACT_FAIL)
+
+/*
+ * Parameters of one step (Sec. 2).
+ *   theta        generalized-minmod parameter, 1 <= theta <= 2 (also bounds
+ *                the hybrid limiter).
+ *   roe_fallback solver used where Roe's linearisation fails: HLLE, HLLC or
+ *                EXACT (Sec. 2).  Ignored for other solvers.
+ *   dt, dx[3]    time step and cell widths.  If dt_dev is non-NULL the step
+ *                reads dt from that device double instead (so a device-side
+ *                CFL reduction can feed it without a host round trip).
+ *   dens_floor, pres_floor  floors applied as max(q, floor) whenever
+ *                primitive variables are recovered (0 disables).
+ *   block_threads  threads per CTA; 0 = the library default (the autotuner
+ *                  sets it).  Must be a multiple of 32 and <= the kernel's
+ *                  maximum (hydro_max_block_threads).
+ *   grid_ctas    CTAs of the persistent launch; 0 = one per SM (x the
+ *                resident count).
+ *   workspace    device scratch for the FP64 kernels (their stage buffers do
+ *                not fit in shared memory); size from hydro_workspace_bytes.
+ *                May be NULL when that size is 0.
+ */
+typedef struct hydro_params {
+  int scheme, recon, limiter, riemann, roe_fallback, precision;
+  double theta, gamma, dt;
+  double dx[3];
+  double dens_floor, pres_floor;
+  const double* dt_dev;
+  int block_threads, grid_ctas;
+  void* workspace;
+  size_t workspace_bytes;
+} hydro_params;
+
+/* Ghost layers the scheme needs (Sec. 2): MHM and CTU 2 (PLM) / 3 (PPM);
+ * VL 3 (PLM) / 4 (PPM).  Returns HYDRO_EINVAL for unknown enums. */
+int hydro_required_ghost(int scheme, int recon);
+
+/* Device scratch (bytes) hydro_advance* needs for this configuration and
+ * launch shape; 0 for the FP32 forms (their stage buffers live in shared
+ * memory). */
+size_t hydro_workspace_bytes(const hydro_params* p, int N);
+
+/* Largest block_threads the (scheme, recon, riemann, precision) kernel was
+ * built for, or a negative error code. */
+int hydro_max_block_threads(const hydro_params* p, int N);
+
+/*
+ * hydro_advance — one step of G patch groups (Sec. 2 steps (1)-(5); Sec. 3.1
+ * one CTA per group, run as a persistent loop over the groups).
+ *   U_in       device [G][5][M][M][M], read only.  Interior + ghost zones.
+ *   U_out      device [G][5][N][N][N]; must not alias U_in.
+ *   flux       device [G][6][5][N][N] or NULL: fluxes through the six faces
+ *              of each group (step (5), for the coarse-fine correction).
+ *   dev_status device unsigned[G] or NULL: HYDRO_ST_* bits of each group.
+ *   G >= 0 (0 is a no-op), N in {8, 16}, ghost >= hydro_required_ghost.
+ */
+int hydro_advance(const hydro_params* p, const void* U_in, void* U_out, void* flux, int G, int N, int ghost,
+                  unsigned* dev_status, void* stream);
+
+/*
+ * hydro_gather_uniform — the preparation step (Sec. 4.2) on the device:
+ * halo-padded groups from a uniform field.
+ *   field   device [5][Z][Y][X] (storage type per precision).
+ *   origin  device int[G][3]: interior corner (x0, y0, z0) of each group.
+ *   bc      HYDRO_BC_PERIODIC or HYDRO_BC_OUTFLOW (zero gradient).
+ *   U_out   device [G][5][M][M][M], M = N + 2*ghost.
+ */
+int hydro_gather_uniform(const void* field, int X, int Y, int Z, int bc, const int* origin, int G, int N, int ghost,
+                         int precision, void* U_out, void* stream);
+
+/*
+ * hydro_advance_uniform — gather fused into the step for a uniform box tiled
+ * by N^3 groups (group index (gz*GY + gy)*GX + gx): every CTA reads its
+ * group's halo straight from field_in with the boundary condition bc and
+ * writes its interior to field_out (double buffering; no aliasing).
+ *   field_in, field_out  device [5][Z][Y][X]; X, Y, Z multiples of N.
+ *   flux, dev_status     as hydro_advance, indexed by that group order.
+ */
+int hydro_advance_uniform(const hydro_params* p, const void* field_in, void* field_out, int X, int Y, int Z, int N,
+                          int bc, void* flux, unsigned* dev_status, void* stream);
+
+/* One entry of a multi-level (or multi-box) batch. */
+typedef struct hydro_level {
+  const void* U_in;     /* groups [G][5][M^3] (mode 0) or field [5][Z][Y][X] (mode 1) */
+  void* U_out;          /* groups [G][5][N^3] (mode 0) or field (mode 1)              */
+  void* flux;           /* [G][6][5][N][N] or NULL                                    */
+  unsigned* status;     /* [G] or NULL                                                */
+  const double* dt_dev; /* optional device dt of this entry (overrides dt)            */
+  double dt;
+  double dx[3];
+  int G;                /* groups (mode 0); ignored in mode 1 (derived from X, Y, Z)  */
+  int mode;             /* 0 = prepared groups, 1 = uniform field with bc             */
+  int bc, X, Y, Z;      /* mode 1 only                                                */
+} hydro_level;
+
+/* Most entries one hydro_advance_levels call accepts. */
+#define HYDRO_MAX_LEVELS 32
+
+/*
+ * hydro_advance_levels — one persistent launch that advances uneven per-AMR-
+ * level group lists (or independent boxes) in one go: the work of all
+ * entries is one flat list of groups shared round-robin by the CTAs.  Every
+ * entry has its own dx and dt; scheme, reconstruction, limiter, solver,
+ * precision and ghost width come from p (p->dt and p->dx are ignored).
+ *   nlev in [0, HYDRO_MAX_LEVELS].
+ */
+int hydro_advance_levels(const hydro_params* p, const hydro_level* levels, int nlev, int N, int ghost, void* stream);
+
+/*
+ * hydro_cfl_dt — evolution time step (Sec. 4.3) as a device reduction:
+ *   dt = cfl / max over cells of max_d (|v_d| + c) / dx_d,  c = sqrt(gamma p / rho),
+ * with primitives recovered with the floors.  The maximum is reduced in FP64
+ * for every precision.
+ *   U        device, element (g, v, i) at U[g*group_stride + v*var_stride + i],
+ *            i < cells, g < G (a field: G = 1, var_stride = cells = X*Y*Z).
+ *   dt_dev   device double[1]: receives dt.  smax_dev (optional) receives the
+ *            maximum signal speed / dx.
+ *   workspace device scratch of hydro_cfl_workspace_bytes() bytes.
+ */
+size_t hydro_cfl_workspace_bytes(void);
+int hydro_cfl_dt(const void* U, int G, long long group_stride, long long var_stride, long long cells, int precision,
+                 double gamma, double dens_floor, double pres_floor, const double* dx, double cfl, double* dt_dev,
+                 double* smax_dev, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * hydro_conserved_totals — global sums of the five conserved variables over
+ * the same addressing as hydro_cfl_dt, accumulated in FP64 (the
+ * conservation check of the mixed-precision form).
+ *   totals_dev  device double[5].
+ */
+int hydro_conserved_totals(const void* U, int G, long long group_stride, long long var_stride, long long cells,
+                           int precision, double* totals_dev, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Text for a return code. */
+const char* hydro_strerror(int code);
+
+/* The last CUDA error string seen by the library on this thread ("" if none). */
+const char* hydro_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

@@ -1,0 +1,149 @@
+// Per-group context of the persistent patch-group kernels (Sec. 3.1: one
+// thread block per patch group; here a persistent loop of each CTA over a
+// flat list of groups that may span several AMR levels or boxes).
+#pragma once
+#include "phys.cuh"
+
+namespace hyd {
+
+constexpr int MAX_SEG = 32;  // == HYDRO_MAX_LEVELS
+
+// One entry of the work list (a level, a box or a plain group batch).
+struct SegDesc {
+  const void* in;       // mode 0: groups [G][5][M^3]; mode 1: field [5][Z][Y][X]
+  void* out;            // mode 0: groups [G][5][N^3]; mode 1: field
+  void* flux;           // [G][6][5][N][N] or null
+  unsigned* status;     // [G] or null
+  const double* dt_dev; // optional device dt
+  double dt;
+  double dx[3];
+  int G, mode, bc, X, Y, Z, GX, GY;
+  int first;            // flat index of this entry's first group
+};
+
+struct WorkTable {
+  int nseg;
+  int total;
+  SegDesc seg[MAX_SEG];
+};
+
+// Launch-wide constants.
+struct KConst {
+  double gamma, dens_floor, pres_floor, theta;
+  int limiter, fallback, ghost;
+  long long ring_elems;  // per-CTA scratch elements (global-memory rings)
+};
+
+// Addressing of one group's input / output and its step constants.
+template <class T, class S, int N> struct GroupCtx {
+  const S* in;
+  S* out;
+  S* flux;
+  int mode, bc, g, M;
+  long long Mpl;  // M*M
+  int X, Y, Z, ox, oy, oz;
+  long long XYZ;
+  T dtdx[3], hdtdx[3];
+  double dtdx_d[3];
+
+  __device__ __forceinline__ void init(const SegDesc& sg, int gi, const KConst& kc) {
+    mode = sg.mode;
+    g = kc.ghost;
+    M = N + 2 * g;
+    Mpl = (long long)M * M;
+    double dt = sg.dt_dev ? *sg.dt_dev : sg.dt;
+    for (int d = 0; d < 3; ++d) {
+      dtdx_d[d] = dt / sg.dx[d];
+      dtdx[d] = (T)dtdx_d[d];
+      hdtdx[d] = (T)(0.5 * dt / sg.dx[d]);
+    }
+    flux = sg.flux ? (S*)sg.flux + (long long)gi * 30 * N * N : nullptr;
+    if (mode == 0) {
+      in = (const S*)sg.in + (long long)gi * 5 * Mpl * M;
+      out = (S*)sg.out + (long long)gi * 5 * N * N * N;
+      bc = 0;
+    } else {
+      in = (const S*)sg.in;
+      out = (S*)sg.out;
+      bc = sg.bc;
+      X = sg.X;
+      Y = sg.Y;
+      Z = sg.Z;
+      XYZ = (long long)X * Y * Z;
+      int gx = gi % sg.GX;
+      int gy = (gi / sg.GX) % sg.GY;
+      int gz = gi / (sg.GX * sg.GY);
+      ox = gx * N;
+      oy = gy * N;
+      oz = gz * N;
+    }
+  }
+
+  __device__ __forceinline__ static int wrap(int a, int n, int bc) {
+    if (bc == 0) {
+      a = a % n;
+      return a < 0 ? a + n : a;
+    }
+    return a < 0 ? 0 : (a >= n ? n - 1 : a);
+  }
+
+  // Input value of variable v at interior coordinates (x, y, z), which may lie
+  // in the ghost zone (-g <= x < N + g).
+  __device__ __forceinline__ T load(int v, int x, int y, int z) const {
+    if (mode == 0) return (T)in[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
+    int sx = wrap(ox + x, X, bc), sy = wrap(oy + y, Y, bc), sz = wrap(oz + z, Z, bc);
+    return (T)in[v * XYZ + ((long long)sz * Y + sy) * X + sx];
+  }
+  __device__ __forceinline__ S load_raw(int v, int x, int y, int z) const {
+    if (mode == 0) return in[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
+    return in[v * XYZ + ((long long)(oz + z) * Y + (oy + y)) * X + (ox + x)];
+  }
+  __device__ __forceinline__ void store(int v, int x, int y, int z, S val) const {
+    if (mode == 0)
+      out[(long long)v * N * N * N + (z * N + y) * N + x] = val;
+    else
+      out[v * XYZ + ((long long)(oz + z) * Y + (oy + y)) * X + (ox + x)] = val;
+  }
+  // Boundary flux of face f (0..5) at transverse indices (a, b).
+  __device__ __forceinline__ void store_flux(int f, int v, int a, int b, T val) const {
+    if (flux) flux[((f * 5 + v) * N + a) * N + b] = (S)val;
+  }
+};
+
+// Slot of plane p in a ring of R planes (p >= -8).
+template <int R> __device__ __forceinline__ int slot(int p) { return (p + 8 * R) % R; }
+
+// Conservative update of one interior cell (step (4)) from the face flux
+// differences dF[d][v] = F(c + e_d/2) - F(c - e_d/2):
+//   U_new = U - ((dtdx0 dF0 + dtdx1 dF1) + dtdx2 dF2),
+// in FP64 for the mixed form; sets the status bits of the new state.
+template <class T, class S, bool MIXED, int N>
+__device__ __forceinline__ unsigned update_cell(const GroupCtx<T, S, N>& C, int x, int y, int z, const T dF[3][5],
+                                                const Gas<T>& gas) {
+  T Un[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    if (MIXED) {
+      double dU = C.dtdx_d[0] * (double)dF[0][v] + C.dtdx_d[1] * (double)dF[1][v] + C.dtdx_d[2] * (double)dF[2][v];
+      Un[v] = (T)((double)C.load_raw(v, x, y, z) - dU);
+    } else {
+      T dU = C.dtdx[0] * dF[0][v] + C.dtdx[1] * dF[1][v] + C.dtdx[2] * dF[2][v];
+      Un[v] = (T)C.load_raw(v, x, y, z) - dU;
+    }
+    C.store(v, x, y, z, (S)Un[v]);
+  }
+  unsigned st = 0;
+  bool nan = false;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) nan = nan || isnanv(Un[v]);
+  if (nan) st |= ST_NAN;
+  if (!(Un[0] > T(0))) {
+    st |= ST_NEG_DENS;
+  } else {
+    T p = gas.gm1 * (Un[4] - T(0.5) * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) / Un[0]);
+    if (!(p > T(0))) st |= ST_NEG_PRES;
+  }
+  return st;
+}
+
+}  // namespace hyd

@@ -1,0 +1,114 @@
+// Persistent patch-group kernel: each CTA walks the flat list of groups of
+// all work-table entries (levels / boxes / one batch) with stride gridDim.x
+// and runs the selected scheme on each (Sec. 3.1: one thread block per patch
+// group; here the blocks are persistent, one per SM).
+#pragma once
+#include "ctu.cuh"
+#include "mhm.cuh"
+#include "vl.cuh"
+
+namespace hyd {
+
+template <int SCH, int REC, int PR, int N> struct KTraits {
+  using P = Prec<PR>;
+  using T = typename P::T;
+  using S = typename P::S;
+  static constexpr int S_ = REC == PPM ? 2 : 1;
+  static constexpr int RING = SCH == CTU ? CtuLayout<N, S_>::TOTAL
+                              : SCH == MHM ? MhmLayout<N, S_>::TOTAL
+                                           : VlLayout<N, S_>::TOTAL;
+  static constexpr bool SMEM = PR != P_FP64;  // FP64 rings do not fit in shared memory
+  static constexpr int MAXT = PR == P_FP64 ? 256 : 384;
+};
+
+template <int SCH, int REC, int RS, int PR, int N>
+__global__ void __launch_bounds__(KTraits<SCH, REC, PR, N>::MAXT, 1)
+    advance_kernel(const __grid_constant__ WorkTable wt, const KConst kc, void* ws) {
+  using Tr = KTraits<SCH, REC, PR, N>;
+  using T = typename Tr::T;
+  using S = typename Tr::S;
+  constexpr bool MIXED = Tr::P::MIXED;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned st_sh;
+  T* ring;
+  if constexpr (Tr::SMEM)
+    ring = reinterpret_cast<T*>(smem_raw);
+  else
+    ring = reinterpret_cast<T*>(ws) + (long long)blockIdx.x * kc.ring_elems;
+  Opts<T> o;
+  o.gas.gamma = (T)kc.gamma;
+  o.gas.gm1 = (T)(kc.gamma - 1.0);
+  o.gas.dens_floor = (T)kc.dens_floor;
+  o.gas.pres_floor = (T)kc.pres_floor;
+  o.theta = (T)kc.theta;
+  o.limiter = kc.limiter;
+  o.fallback = kc.fallback;
+  if (threadIdx.x == 0) st_sh = 0;
+  for (int w = blockIdx.x; w < wt.total; w += gridDim.x) {
+    int s = 0;
+    while (s + 1 < wt.nseg && w >= wt.seg[s + 1].first) ++s;
+    const SegDesc& sg = wt.seg[s];
+    const int gi = w - sg.first;
+    GroupCtx<T, S, N> C;
+    C.init(sg, gi, kc);
+    __syncthreads();
+    if constexpr (SCH == CTU)
+      ctu_group<T, S, MIXED, RS, REC, N>(C, o, ring, st_sh);
+    else if constexpr (SCH == MHM)
+      mhm_group<T, S, MIXED, RS, REC, N>(C, o, ring, st_sh);
+    else
+      vl_group<T, S, MIXED, RS, REC, N>(C, o, ring, st_sh);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (sg.status) sg.status[gi] = st_sh;
+      st_sh = 0;
+    }
+  }
+}
+
+// Host-side description of one compiled kernel.
+struct KernelEntry {
+  const void* fn;
+  long long ring_elems;
+  int elem_bytes;
+  int max_threads;
+  int smem;  // 1: rings in shared memory
+};
+
+constexpr int NKEY = 3 * 2 * 4 * 3;
+inline int kernel_key(int sch, int rec, int rs, int pr) { return ((sch * 2 + rec) * 4 + rs) * 3 + pr; }
+
+template <int SCH, int REC, int RS, int PR, int N> inline void put_kernel(KernelEntry* tab) {
+  using Tr = KTraits<SCH, REC, PR, N>;
+  KernelEntry& e = tab[kernel_key(SCH, REC, RS, PR)];
+  e.fn = (const void*)&advance_kernel<SCH, REC, RS, PR, N>;
+  e.ring_elems = Tr::RING;
+  e.elem_bytes = (int)sizeof(typename Tr::T);
+  e.max_threads = Tr::MAXT;
+  e.smem = Tr::SMEM ? 1 : 0;
+}
+
+template <int SCH, int PR, int N> inline void put_scheme(KernelEntry* tab) {
+  put_kernel<SCH, PLM, RS_EXACT, PR, N>(tab);
+  put_kernel<SCH, PLM, RS_HLLE, PR, N>(tab);
+  put_kernel<SCH, PLM, RS_HLLC, PR, N>(tab);
+  put_kernel<SCH, PLM, RS_ROE, PR, N>(tab);
+  put_kernel<SCH, PPM, RS_EXACT, PR, N>(tab);
+  put_kernel<SCH, PPM, RS_HLLE, PR, N>(tab);
+  put_kernel<SCH, PPM, RS_HLLC, PR, N>(tab);
+  put_kernel<SCH, PPM, RS_ROE, PR, N>(tab);
+}
+
+}  // namespace hyd
+
+// Registration functions, one per (scheme, precision) translation unit.
+#define HYD_DECLARE_REG(name) void name(hyd::KernelEntry* tab)
+HYD_DECLARE_REG(hyd_reg_mhm_fp64);
+HYD_DECLARE_REG(hyd_reg_mhm_fp32);
+HYD_DECLARE_REG(hyd_reg_mhm_mixed);
+HYD_DECLARE_REG(hyd_reg_vl_fp64);
+HYD_DECLARE_REG(hyd_reg_vl_fp32);
+HYD_DECLARE_REG(hyd_reg_vl_mixed);
+HYD_DECLARE_REG(hyd_reg_ctu_fp64);
+HYD_DECLARE_REG(hyd_reg_ctu_fp32);
+HYD_DECLARE_REG(hyd_reg_ctu_mixed);

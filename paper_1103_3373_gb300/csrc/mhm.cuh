@@ -1,0 +1,102 @@
+// MUSCL-Hancock (MHM, Sec. 2) for one patch group, streamed along z.
+//
+// Sec. 2: the half-step face values are obtained from the reconstructed face
+// values with their physical fluxes (no Riemann solver), advanced by dt/2 with
+// the flux differences of all three directions; Sec. 3.1: all six face values
+// of a cell are evaluated before moving to the next cell, so the fluxes stay
+// in registers.  Then 3 Riemann solves per cell and the update.
+//
+// Iteration t:  F  update of plane pB-2 (completed by the previous iteration)
+//               A  load plane pA = t-1-S as primitives
+//               B  reconstruct + predict the 6 face states of the cells
+//                  [-1,N]^2 of plane pB = pA-S
+//               C  final fluxes: x/y faces of plane pB, z faces below it
+#pragma once
+#include "stages.cuh"
+
+namespace hyd {
+
+template <int N, int S> struct MhmLayout {
+  static constexpr int L = N + 2;
+  static constexpr int LW = N + 2 + 2 * S;
+  using WR = PlaneRing<float, LW, 2 * S + 1>;
+  using FRf = FaceRings<float, N, 1, 2>;
+  static constexpr int OFF_FR = WR::ELEMS;
+  static constexpr int TOTAL = OFF_FR + FRf::ELEMS;
+};
+
+// Physical flux along d of a global-frame face state (W primitive, U its
+// conserved form; energy U[4]).
+template <class T> __device__ __forceinline__ void pflux_global(const T W[5], const T U[5], int d, T F[5]) {
+  T wl[5], fl[5];
+  rot_in(W, wl, d);
+  pflux(wl, U[4], fl);
+  rot_out(fl, F, d);
+}
+
+template <class T, class S, bool MIXED, int RS, int REC, int N>
+__device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
+  constexpr int S_ = REC == PPM ? 2 : 1;
+  using Lay = MhmLayout<N, S_>;
+  constexpr int L = Lay::L, LL = L * L, LW = Lay::LW;
+  PlaneRing<T, LW, 2 * S_ + 1> Wr{ring};
+  FaceRings<T, N, 1, 2> R{ring + Lay::OFF_FR};
+  unsigned st = 0;
+  const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
+
+  constexpr int T_ITERS = N + 3 + 2 * S_;
+  for (int t = 0; t < T_ITERS; ++t) {
+    const int pA = t - 1 - S_;
+    const int pB = pA - S_;
+    const int pF = pB - 2;
+    if (pF >= 0 && pF < N) st |= stage_update<T, S, MIXED, N>(C, o, R, pF);
+    if (pA <= N + S_) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, pA, 1 + S_, Wr);
+    __syncthreads();
+
+    // B: reconstruction + half-step prediction of the cells of plane pB
+    if (pB >= -1 && pB <= N) {
+      for (int idx = threadIdx.x; idx < LL; idx += blockDim.x) {
+        int jj = idx / L, ii = idx - jj * L;
+        T Uf[3][2][5], Ff[3][2][5];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          T w[5][5], Wf[2][5], dW[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+#pragma unroll
+            for (int o2 = -S_; o2 <= S_; ++o2) {
+              if (d == 0) w[v][o2 + 2] = Wr(pB, v, jj + S_, ii + S_ + o2);
+              else if (d == 1) w[v][o2 + 2] = Wr(pB, v, jj + S_ + o2, ii + S_);
+              else w[v][o2 + 2] = Wr(pB + o2, v, jj + S_, ii + S_);
+            }
+          }
+          recon5<REC>(w, o, Wf[0], Wf[1], dW);
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            cons(Wf[s], Uf[d][s], o.gas);
+            pflux_global(Wf[s], Uf[d][s], d, Ff[d][s]);
+          }
+        }
+        // S = dt/(2dx) (Fx(R) - Fx(L)) + dt/(2dy) (...) + dt/(2dz) (...)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          T Sv = h0 * (Ff[0][1][v] - Ff[0][0][v]) + h1 * (Ff[1][1][v] - Ff[1][0][v]) + h2 * (Ff[2][1][v] - Ff[2][0][v]);
+          R.XY(pB, 0, 0, v, jj, ii) = Uf[0][0][v] - Sv;
+          R.XY(pB, 0, 1, v, jj, ii) = Uf[0][1][v] - Sv;
+          R.XY(pB, 1, 0, v, jj, ii) = Uf[1][0][v] - Sv;
+          R.XY(pB, 1, 1, v, jj, ii) = Uf[1][1][v] - Sv;
+          R.Zs(pB, 0, v, jj, ii) = Uf[2][0][v] - Sv;
+          R.Zs(pB, 1, v, jj, ii) = Uf[2][1][v] - Sv;
+        }
+      }
+    }
+    __syncthreads();
+
+    // C: 3 Riemann solves per cell (x/y faces of plane pB, z faces below it)
+    if (pB >= 0 && pB <= N) st |= stage_flux2<T, S, MIXED, RS, N>(C, o, R, pB);
+    __syncthreads();
+  }
+  if (st) atomicOr(&st_sh, st);
+}
+
+}  // namespace hyd

@@ -1,0 +1,170 @@
+// Stages shared by the three plane-streaming group kernels (MHM, VL, CTU):
+// ring-buffer addressing of the face states and final fluxes, the final
+// Riemann solves of one plane with the group-boundary flux store (Sec. 2
+// steps (2)/(3) and (5)), the conservative update of one plane (step (4)),
+// and the load of one input plane.
+//
+// Ring planes are addressed by their z index p; a ring of depth R keeps
+// planes p, p-1, ..., p-R+1.  Within a plane the layout is [var][row][col]
+// so that consecutive threads touch consecutive words.
+#pragma once
+#include "group.cuh"
+
+namespace hyd {
+
+// Face states (conserved, after prediction / tracing / correction) and the
+// final fluxes of one group.
+//   XY: [dir x|y][side L|R][var][L][L], cells [-1,N]^2 of the plane
+//   Z : [side][var][L][L]
+//   F2x: [var][N rows][N+1 faces]   (face f between cells f-1 and f)
+//   F2y: [var][N+1 faces][N cols]
+//   F2z: [var][N][N], the faces below plane p
+template <class T, int N, int DXY, int DZ> struct FaceRings {
+  static constexpr int L = N + 2, LL = L * L;
+  static constexpr int XYPL = 2 * 2 * 5 * LL;
+  static constexpr int ZPL = 2 * 5 * LL;
+  static constexpr int F2X = 5 * N * (N + 1);
+  static constexpr int F2XYPL = 2 * F2X;
+  static constexpr int F2ZPL = 5 * N * N;
+  static constexpr int ELEMS = DXY * XYPL + DZ * ZPL + 2 * F2XYPL + 2 * F2ZPL;
+  T* base;
+  __device__ __forceinline__ T& XY(int p, int dir, int side, int v, int jj, int ii) const {
+    return base[slot<DXY>(p) * XYPL + (((dir * 2 + side) * 5 + v) * L + jj) * L + ii];
+  }
+  __device__ __forceinline__ T& Zs(int p, int side, int v, int jj, int ii) const {
+    return base[DXY * XYPL + slot<DZ>(p) * ZPL + ((side * 5 + v) * L + jj) * L + ii];
+  }
+  __device__ __forceinline__ T& F2x(int p, int v, int j, int f) const {
+    return base[DXY * XYPL + DZ * ZPL + slot<2>(p) * F2XYPL + (v * N + j) * (N + 1) + f];
+  }
+  __device__ __forceinline__ T& F2y(int p, int v, int f, int i) const {
+    return base[DXY * XYPL + DZ * ZPL + slot<2>(p) * F2XYPL + F2X + (v * (N + 1) + f) * N + i];
+  }
+  __device__ __forceinline__ T& F2z(int p, int v, int j, int i) const {
+    return base[DXY * XYPL + DZ * ZPL + 2 * F2XYPL + slot<2>(p) * F2ZPL + (v * N + j) * N + i];
+  }
+};
+
+// Final Riemann solves of plane p: x and y faces of the interior cells of
+// plane p (if 0 <= p < N) and the z faces between planes p-1 and p (if
+// 0 <= p <= N).  Fluxes on the group boundary are stored at once (step (5)).
+template <class T, class S, bool MIXED, int RS, int N, class FR>
+__device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p) {
+  unsigned st = 0;
+  const int nx = (p < N) ? N * (N + 1) : 0;
+  const int cnt = 2 * nx + N * N;
+  for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+    T UL[5], UR[5], F[5];
+    if (idx < nx) {
+      int j = idx / (N + 1), f = idx - j * (N + 1);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        UL[v] = R.XY(p, 0, 1, v, j + 1, f);
+        UR[v] = R.XY(p, 0, 0, v, j + 1, f + 1);
+      }
+      st |= riemann<T, MIXED, RS>(0, UL, UR, o, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) R.F2x(p, v, j, f) = F[v];
+      if (f == 0 || f == N) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 0 : 1, v, p, j, F[v]);
+      }
+    } else if (idx < 2 * nx) {
+      int k = idx - nx;
+      int f = k / N, i = k - f * N;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        UL[v] = R.XY(p, 1, 1, v, f, i + 1);
+        UR[v] = R.XY(p, 1, 0, v, f + 1, i + 1);
+      }
+      st |= riemann<T, MIXED, RS>(1, UL, UR, o, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) R.F2y(p, v, f, i) = F[v];
+      if (f == 0 || f == N) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 2 : 3, v, p, i, F[v]);
+      }
+    } else {
+      int k = idx - 2 * nx;
+      int j = k / N, i = k - j * N;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        UL[v] = R.Zs(p - 1, 1, v, j + 1, i + 1);
+        UR[v] = R.Zs(p, 0, v, j + 1, i + 1);
+      }
+      st |= riemann<T, MIXED, RS>(2, UL, UR, o, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) R.F2z(p, v, j, i) = F[v];
+      if (p == 0 || p == N) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) C.store_flux(p == 0 ? 4 : 5, v, j, i, F[v]);
+      }
+    }
+  }
+  return st;
+}
+
+// Conservative update of plane p from the final fluxes (step (4)).
+template <class T, class S, bool MIXED, int N, class FR>
+__device__ __forceinline__ unsigned stage_update(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p) {
+  unsigned st = 0;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int j = idx / N, i = idx - j * N;
+    T dF[3][5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      dF[0][v] = R.F2x(p, v, j, i + 1) - R.F2x(p, v, j, i);
+      dF[1][v] = R.F2y(p, v, j + 1, i) - R.F2y(p, v, j, i);
+      dF[2][v] = R.F2z(p + 1, v, j, i) - R.F2z(p, v, j, i);
+    }
+    st |= update_cell<T, S, MIXED, N>(C, i, j, p, dF, o.gas);
+  }
+  return st;
+}
+
+// Ring of LW x LW input planes; the plane's lateral index ii maps to the
+// interior coordinate ii - off.
+template <class T, int LW, int R> struct PlaneRing {
+  static constexpr int PL = 5 * LW * LW;
+  static constexpr int ELEMS = R * PL;
+  T* base;
+  __device__ __forceinline__ T& operator()(int p, int v, int jj, int ii) const {
+    return base[slot<R>(p) * PL + (v * LW + jj) * LW + ii];
+  }
+};
+
+// Load plane p into a ring, as primitives (PRIM) or conserved variables.
+template <bool PRIM, class T, class S, bool MIXED, int N, int LW, int R>
+__device__ __forceinline__ void stage_load(const GroupCtx<T, S, N>& C, const Opts<T>& o, int p, int off,
+                                           const PlaneRing<T, LW, R>& ring) {
+  for (int idx = threadIdx.x; idx < LW * LW; idx += blockDim.x) {
+    int jj = idx / LW, ii = idx - jj * LW;
+    T U[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = C.load(v, ii - off, jj - off, p);
+    if (PRIM) {
+      T W[5];
+      prim<T, MIXED>(U, W, o.gas);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) ring(p, v, jj, ii) = W[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) ring(p, v, jj, ii) = U[v];
+    }
+  }
+}
+
+// Face values of one cell along d from a primitive ring (Sec. 2 step (1)):
+// w[] = the 2S+1 stencil values per variable, centre at index 2.
+template <int REC, class T>
+__device__ __forceinline__ void recon5(const T w[5][5], const Opts<T>& o, T WLf[5], T WRf[5], T dW[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    if (REC == PPM)
+      ppm(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4], o.limiter, o.theta, WLf[v], WRf[v]);
+    else
+      plm(w[v][1], w[v][2], w[v][3], o.limiter, o.theta, WLf[v], WRf[v], dW[v]);
+  }
+}
+
+}  // namespace hyd

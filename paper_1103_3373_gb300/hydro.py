@@ -1,0 +1,279 @@
+"""Python binding of libhydro (include/hydro.h): argument marshalling only.
+
+Each function has the name of the C entry point it calls and takes torch CUDA
+tensors (device memory and streams come from PyTorch); every step of the
+computation runs in the library's kernels.  There is no CPU fallback: if
+libhydro.so is missing or no GPU is present the calls raise.
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhydro.so")
+
+# enumerations (include/hydro.h; Sec. 2 of the paper)
+MHM, VL, CTU = 0, 1, 2
+PLM, PPM = 0, 1
+LIM_MINMOD, LIM_VANLEER, LIM_VANALBADA, LIM_HYBRID = 0, 1, 2, 3
+RS_EXACT, RS_HLLE, RS_HLLC, RS_ROE = 0, 1, 2, 3
+FP64, FP32, FP32_MIXED = 0, 1, 2
+BC_PERIODIC, BC_OUTFLOW = 0, 1
+OK, EINVAL, EGHOST, EUNSUPPORTED, ECUDA, EWORKSPACE = 0, -1, -2, -3, -4, -5
+ST_ROE_FALLBACK, ST_NEG_DENS, ST_NEG_PRES, ST_NAN, ST_EXACT_FAIL = 1, 2, 4, 8, 16
+ST_ERROR_MASK = ST_NEG_DENS | ST_NEG_PRES | ST_NAN | ST_EXACT_FAIL
+MAX_LEVELS = 32
+
+SCHEMES = {"mhm": MHM, "vl": VL, "ctu": CTU}
+RECONS = {"plm": PLM, "ppm": PPM}
+SOLVERS = {"exact": RS_EXACT, "hlle": RS_HLLE, "hllc": RS_HLLC, "roe": RS_ROE}
+LIMITERS = {"minmod": LIM_MINMOD, "vanleer": LIM_VANLEER, "vanalbada": LIM_VANALBADA, "hybrid": LIM_HYBRID}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": FP32_MIXED}
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code, where):
+        msg = "%s: %s" % (where, _lib().hydro_strerror(code).decode())
+        if code == ECUDA:
+            msg += " (%s)" % _lib().hydro_last_cuda_error().decode()
+        super().__init__(msg)
+        self.code = code
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("recon", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("riemann", ctypes.c_int), ("roe_fallback", ctypes.c_int), ("precision", ctypes.c_int),
+                ("theta", ctypes.c_double), ("gamma", ctypes.c_double), ("dt", ctypes.c_double),
+                ("dx", ctypes.c_double * 3), ("dens_floor", ctypes.c_double), ("pres_floor", ctypes.c_double),
+                ("dt_dev", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class _CLevel(ctypes.Structure):
+    _fields_ = [("U_in", ctypes.c_void_p), ("U_out", ctypes.c_void_p), ("flux", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("dt_dev", ctypes.c_void_p), ("dt", ctypes.c_double),
+                ("dx", ctypes.c_double * 3), ("G", ctypes.c_int), ("mode", ctypes.c_int), ("bc", ctypes.c_int),
+                ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int)]
+
+
+@dataclass
+class Params:
+    """hydro_params.  dt_dev / workspace are torch tensors (or None)."""
+    scheme: int = CTU
+    recon: int = PPM
+    limiter: int = LIM_MINMOD
+    riemann: int = RS_ROE
+    roe_fallback: int = RS_HLLE
+    precision: int = FP32
+    theta: float = 1.0
+    gamma: float = 1.4
+    dt: float = 0.0
+    dx: tuple = field(default_factory=lambda: (1.0, 1.0, 1.0))
+    dens_floor: float = 0.0
+    pres_floor: float = 0.0
+    dt_dev: object = None
+    block_threads: int = 0
+    grid_ctas: int = 0
+    workspace: object = None
+
+    def c(self):
+        p = _CParams()
+        for k in ("scheme", "recon", "limiter", "riemann", "roe_fallback", "precision", "block_threads",
+                  "grid_ctas"):
+            setattr(p, k, int(getattr(self, k)))
+        for k in ("theta", "gamma", "dt", "dens_floor", "pres_floor"):
+            setattr(p, k, float(getattr(self, k)))
+        for d in range(3):
+            p.dx[d] = float(self.dx[d])
+        p.dt_dev = _ptr(self.dt_dev, "dt_dev", dtype="float64") if self.dt_dev is not None else None
+        if self.workspace is not None:
+            p.workspace = self.workspace.data_ptr()
+            p.workspace_bytes = self.workspace.numel() * self.workspace.element_size()
+        return p
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhydro.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, ll, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+        P = ctypes.POINTER(_CParams)
+        L.hydro_required_ghost.argtypes = [i, i]
+        L.hydro_workspace_bytes.argtypes = [P, i]
+        L.hydro_workspace_bytes.restype = ctypes.c_size_t
+        L.hydro_max_block_threads.argtypes = [P, i]
+        L.hydro_advance.argtypes = [P, vp, vp, vp, i, i, i, vp, vp]
+        L.hydro_advance_uniform.argtypes = [P, vp, vp, i, i, i, i, i, vp, vp, vp]
+        L.hydro_advance_levels.argtypes = [P, ctypes.POINTER(_CLevel), i, i, i, vp]
+        L.hydro_gather_uniform.argtypes = [vp, i, i, i, i, vp, i, i, i, i, vp, vp]
+        L.hydro_cfl_workspace_bytes.argtypes = []
+        L.hydro_cfl_workspace_bytes.restype = ctypes.c_size_t
+        L.hydro_cfl_dt.argtypes = [vp, i, ll, ll, ll, i, d, d, d, ctypes.POINTER(ctypes.c_double), d, vp, vp, vp,
+                                   ctypes.c_size_t, vp]
+        L.hydro_conserved_totals.argtypes = [vp, i, ll, ll, ll, i, vp, vp, ctypes.c_size_t, vp]
+        L.hydro_strerror.argtypes = [i]
+        L.hydro_strerror.restype = ctypes.c_char_p
+        L.hydro_last_cuda_error.argtypes = []
+        L.hydro_last_cuda_error.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def library():
+    """The loaded ctypes library (loads it on first use)."""
+    return _lib()
+
+
+def _storage_dtype(precision):
+    return "float64" if precision == FP64 else "float32"
+
+
+def _ptr(t, name, dtype=None):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    if dtype is not None and str(t.dtype).split(".")[-1] != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise HydroError(rc, where)
+
+
+def hydro_required_ghost(scheme, recon):
+    return _lib().hydro_required_ghost(int(scheme), int(recon))
+
+
+def hydro_workspace_bytes(params: Params, N=16):
+    return int(_lib().hydro_workspace_bytes(ctypes.byref(params.c()), N))
+
+
+def hydro_max_block_threads(params: Params, N=16):
+    return int(_lib().hydro_max_block_threads(ctypes.byref(params.c()), N))
+
+
+def hydro_advance(params: Params, U_in, U_out, flux=None, status=None, N=16, ghost=None, stream=None):
+    """One step of the groups in U_in [G,5,M,M,M] -> U_out [G,5,N,N,N]."""
+    dt = _storage_dtype(params.precision)
+    G = U_in.shape[0]
+    M = U_in.shape[-1]
+    g = (M - N) // 2 if ghost is None else ghost
+    rc = _lib().hydro_advance(ctypes.byref(params.c()), _ptr(U_in, "U_in", dt), _ptr(U_out, "U_out", dt),
+                              _ptr(flux, "flux", dt), G, N, g, _ptr(status, "status", "int32"), _stream(stream))
+    _check(rc, "hydro_advance")
+
+
+def hydro_advance_uniform(params: Params, field_in, field_out, bc=BC_PERIODIC, flux=None, status=None, N=16,
+                          stream=None):
+    """One step of a uniform box [5,Z,Y,X] tiled by N^3 groups, gather fused."""
+    dt = _storage_dtype(params.precision)
+    _, Z, Y, X = field_in.shape
+    rc = _lib().hydro_advance_uniform(ctypes.byref(params.c()), _ptr(field_in, "field_in", dt),
+                                      _ptr(field_out, "field_out", dt), X, Y, Z, N, bc, _ptr(flux, "flux", dt),
+                                      _ptr(status, "status", "int32"), _stream(stream))
+    _check(rc, "hydro_advance_uniform")
+
+
+@dataclass
+class Level:
+    """One hydro_level entry: prepared groups (mode 0) or a uniform field (mode 1)."""
+    U_in: object
+    U_out: object
+    dx: tuple
+    dt: float = 0.0
+    dt_dev: object = None
+    flux: object = None
+    status: object = None
+    mode: int = 0
+    bc: int = BC_PERIODIC
+
+
+def make_levels(levels, precision):
+    dt = _storage_dtype(precision)
+    arr = (_CLevel * max(1, len(levels)))()
+    for k, lv in enumerate(levels):
+        c = arr[k]
+        c.U_in = _ptr(lv.U_in, "U_in", dt)
+        c.U_out = _ptr(lv.U_out, "U_out", dt)
+        c.flux = _ptr(lv.flux, "flux", dt)
+        c.status = _ptr(lv.status, "status", "int32")
+        c.dt_dev = _ptr(lv.dt_dev, "dt_dev", "float64")
+        c.dt = float(lv.dt)
+        for d in range(3):
+            c.dx[d] = float(lv.dx[d])
+        c.mode = int(lv.mode)
+        if lv.mode == 0:
+            c.G = lv.U_in.shape[0]
+        else:
+            c.bc = int(lv.bc)
+            _, c.Z, c.Y, c.X = (int(s) for s in lv.U_in.shape)
+    return arr
+
+
+def hydro_advance_levels(params: Params, levels, N=16, ghost=3, stream=None, _carray=None):
+    """One persistent launch over all entries of `levels` (list of Level)."""
+    if len(levels) > MAX_LEVELS:
+        raise ValueError("at most %d entries per call" % MAX_LEVELS)
+    arr = _carray if _carray is not None else make_levels(levels, params.precision)
+    rc = _lib().hydro_advance_levels(ctypes.byref(params.c()), arr, len(levels), N, ghost, _stream(stream))
+    _check(rc, "hydro_advance_levels")
+
+
+def hydro_gather_uniform(field, origins, U_out, N=16, ghost=3, bc=BC_PERIODIC, precision=FP32, stream=None):
+    dt = _storage_dtype(precision)
+    _, Z, Y, X = field.shape
+    G = origins.shape[0]
+    rc = _lib().hydro_gather_uniform(_ptr(field, "field", dt), X, Y, Z, bc, _ptr(origins, "origins", "int32"), G, N,
+                                     ghost, precision, _ptr(U_out, "U_out", dt), _stream(stream))
+    _check(rc, "hydro_gather_uniform")
+
+
+def hydro_cfl_workspace_bytes():
+    return int(_lib().hydro_cfl_workspace_bytes())
+
+
+def _red_layout(U):
+    """(G, group_stride, var_stride, cells) of a field [5,...] or groups [G,5,...]."""
+    if U.shape[0] == 5 and U.dim() in (2, 4):
+        cells = U[0].numel()
+        return 1, 5 * cells, cells, cells
+    G = U.shape[0]
+    cells = U[0, 0].numel()
+    return G, 5 * cells, cells, cells
+
+
+def hydro_cfl_dt(U, dx, cfl, dt_out, workspace, gamma=1.4, dens_floor=0.0, pres_floor=0.0, precision=FP32,
+                 smax_out=None, stream=None):
+    dt = _storage_dtype(precision)
+    G, gs, vs, cells = _red_layout(U)
+    dxa = (ctypes.c_double * 3)(*[float(a) for a in dx])
+    rc = _lib().hydro_cfl_dt(_ptr(U, "U", dt), G, gs, vs, cells, precision, gamma, dens_floor, pres_floor, dxa,
+                             float(cfl), _ptr(dt_out, "dt_out", "float64"), _ptr(smax_out, "smax_out", "float64"),
+                             workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "hydro_cfl_dt")
+
+
+def hydro_conserved_totals(U, totals_out, workspace, precision=FP32, stream=None):
+    dt = _storage_dtype(precision)
+    G, gs, vs, cells = _red_layout(U)
+    rc = _lib().hydro_conserved_totals(_ptr(U, "U", dt), G, gs, vs, cells, precision,
+                                       _ptr(totals_out, "totals_out", "float64"), workspace.data_ptr(),
+                                       workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "hydro_conserved_totals")

@@ -1,0 +1,245 @@
+"""GPU tests of the other entry points and of the edge cases, through the C ABI.
+
+* gather (Sec. 4.2 preparation step) is bit-exact against the oracle's gather;
+* the fused uniform path and the multi-level batch give exactly the bytes of
+  gather + hydro_advance on the same groups;
+* the CFL reduction (Sec. 4.3) and the FP64 totals match the oracle / numpy;
+* edge cases: no groups, one group, a ragged count, tuning shapes, argument
+  errors;
+* the plain-method workload (Sod along x, 32^3 FP64, MHM + PLM minmod + Roe,
+  10 steps at CFL 0.5) stays on the oracle step after step;
+* at full size (256^3, 4096 groups) sampled groups are checked one by one
+  against the oracle, and the whole box against conservation.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1103_3373_gb300 import hydro as H
+from paper_1103_3373_gb300 import workloads as W
+from tests.gpu_common import (TOL_FP32, TOL_FP64, gpu_advance, lognormal_groups, ndtype, params_pair, quantise,
+                              rel_l1, tdtype, with_workspace)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    assert torch.cuda.is_available()
+    return torch, torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("prec", [H.FP64, H.FP32])
+def test_gather_bit_exact(torch_dev, bc, prec):
+    torch, dev = torch_dev
+    rng = np.random.default_rng(2)
+    f = rng.normal(size=(5, 32, 48, 64)).astype(ndtype(prec)).astype(np.float64)
+    N, g = 16, 4
+    orig = W.group_origins(64, 48, 32, N)
+    ref = O.gather(f, orig, N, g, bc=bc)
+    ft = torch.tensor(f, dtype=tdtype(prec), device=dev)
+    ot = torch.tensor(orig, dtype=torch.int32, device=dev)
+    out = torch.empty(ref.shape, dtype=tdtype(prec), device=dev)
+    H.hydro_gather_uniform(ft, ot, out, N=N, ghost=g, bc=bc, precision=prec)
+    np.testing.assert_array_equal(out.double().cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("prec", [H.FP64, H.FP32, H.FP32_MIXED])
+@pytest.mark.parametrize("scheme,recon,rs", [(O.CTU, O.PPM, O.ROE), (O.VL, O.PLM, O.HLLC), (O.MHM, O.PPM, O.HLLE)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fused_uniform_equals_gather_then_advance(torch_dev, prec, scheme, recon, rs, bc):
+    torch, dev = torch_dev
+    n, N = 32, 16
+    g = O.required_ghost(scheme, recon)
+    U = quantise(W.lognormal(n, seed=3, mach=1.2), prec)
+    dx = (1.0 / n,) * 3
+    dt = O.cfl_dt(U, dx, 0.4)
+    _, ph = params_pair(scheme, recon, rs, prec, dt, dx)
+    with_workspace(ph, dev)
+    dtp = tdtype(prec)
+    ft = torch.tensor(U, dtype=dtp, device=dev)
+    orig = torch.tensor(W.group_origins(n, n, n, N), dtype=torch.int32, device=dev)
+    G = orig.shape[0]
+    M = N + 2 * g
+    Ug = torch.empty((G, 5, M, M, M), dtype=dtp, device=dev)
+    H.hydro_gather_uniform(ft, orig, Ug, N=N, ghost=g, bc=bc, precision=prec)
+    Uo = torch.empty((G, 5, N, N, N), dtype=dtp, device=dev)
+    fl = torch.empty((G, 6, 5, N, N), dtype=dtp, device=dev)
+    st = torch.empty(G, dtype=torch.int32, device=dev)
+    H.hydro_advance(ph, Ug, Uo, fl, st)
+    out = torch.empty_like(ft)
+    fl2 = torch.empty_like(fl)
+    st2 = torch.empty_like(st)
+    H.hydro_advance_uniform(ph, ft, out, bc=bc, flux=fl2, status=st2)
+    torch.cuda.synchronize()
+    a = W.scatter_groups(Uo.double().cpu().numpy(), n, n, n)
+    np.testing.assert_array_equal(out.double().cpu().numpy(), a)
+    np.testing.assert_array_equal(fl2.cpu().numpy(), fl.cpu().numpy())
+    np.testing.assert_array_equal(st2.cpu().numpy(), st.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", [H.FP64, H.FP32])
+def test_levels_batch_equals_separate_launches(torch_dev, prec):
+    """Uneven per-level group lists with per-level dx and dt in one persistent
+    launch give the same bytes as one launch per level."""
+    torch, dev = torch_dev
+    N, g = 16, 3
+    dtp = tdtype(prec)
+    sizes = [7, 3, 12, 1]
+    levels, sep = [], []
+    _, ph = params_pair(O.CTU, O.PPM, O.ROE, prec, 0.0, (1, 1, 1))
+    with_workspace(ph, dev)
+    for l, G in enumerate(sizes):
+        _, Ug = lognormal_groups(n=32, N=N, g=g, seed=10 + l, prec=prec)
+        Ug = np.concatenate([Ug] * 2)[:G]
+        dxl = (1.0 / (32 * 2 ** l),) * 3
+        dtl = O.cfl_dt(Ug[:, :, g:-g, g:-g, g:-g], dxl, 0.4)
+        U_in = torch.tensor(Ug, dtype=dtp, device=dev)
+        outs = [torch.empty((G, 5, N, N, N), dtype=dtp, device=dev) for _ in range(2)]
+        fls = [torch.empty((G, 6, 5, N, N), dtype=dtp, device=dev) for _ in range(2)]
+        sts = [torch.empty(G, dtype=torch.int32, device=dev) for _ in range(2)]
+        levels.append(H.Level(U_in=U_in, U_out=outs[0], flux=fls[0], status=sts[0], dx=dxl, dt=dtl))
+        sep.append((U_in, outs[1], fls[1], sts[1], dxl, dtl))
+    H.hydro_advance_levels(ph, levels, N=N, ghost=g)
+    for U_in, out, fl, st, dxl, dtl in sep:
+        ph.dx, ph.dt = dxl, dtl
+        H.hydro_advance(ph, U_in, out, fl, st)
+    torch.cuda.synchronize()
+    for lv, s in zip(levels, sep):
+        np.testing.assert_array_equal(lv.U_out.cpu().numpy(), s[1].cpu().numpy())
+        np.testing.assert_array_equal(lv.flux.cpu().numpy(), s[2].cpu().numpy())
+        np.testing.assert_array_equal(lv.status.cpu().numpy(), s[3].cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", [H.FP64, H.FP32])
+def test_cfl_dt_and_totals(torch_dev, prec):
+    torch, dev = torch_dev
+    U = quantise(W.lognormal(32, seed=5, mach=2.0), prec)
+    dx = (1 / 32, 1 / 24, 1 / 40)
+    ref = O.cfl_dt(U, dx, 0.45)
+    ft = torch.tensor(U, dtype=tdtype(prec), device=dev)
+    ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    H.hydro_cfl_dt(ft, dx, 0.45, dt, ws, precision=prec)
+    assert dt.item() == ref  # FP64 reduction of the same per-cell values: exact
+    tot = torch.zeros(5, dtype=torch.float64, device=dev)
+    H.hydro_conserved_totals(ft, tot, ws, precision=prec)
+    np.testing.assert_allclose(tot.cpu().numpy(), U.reshape(5, -1).sum(axis=1), rtol=1e-13)
+    # grouped layout [G,5,N,N,N]
+    Ug = W.group_origins(32, 32, 32, 16)
+    Ugr = np.stack([U[:, z:z + 16, y:y + 16, x:x + 16] for x, y, z in Ug])
+    gt = torch.tensor(Ugr, dtype=tdtype(prec), device=dev)
+    dt2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    H.hydro_cfl_dt(gt, dx, 0.45, dt2, ws, precision=prec)
+    assert dt2.item() == ref
+
+
+def test_edge_cases_and_errors(torch_dev):
+    torch, dev = torch_dev
+    N = 16
+    po, ph = params_pair(O.CTU, O.PPM, O.ROE, H.FP32, 1e-3, (1 / 32,) * 3)
+    # no groups: a no-op that still validates its arguments
+    empty = torch.empty((0, 5, 22, 22, 22), dtype=torch.float32, device=dev)
+    out0 = torch.empty((0, 5, N, N, N), dtype=torch.float32, device=dev)
+    H.hydro_advance(ph, empty, out0)
+    # one group and a ragged count
+    for G in (1, 7):
+        Uq, Ug = lognormal_groups(n=32, g=3, seed=6, prec=H.FP32)
+        Ug = np.concatenate([Ug] * 2)[:G]
+        ref, ref_flux, _ = O.advance(po, Ug, N)
+        got, flux, _ = gpu_advance(ph, Ug)
+        assert rel_l1(got, ref) <= TOL_FP32
+    # launch shapes: fewer threads, small grids (more groups per CTA)
+    Uq, Ug = lognormal_groups(n=32, g=3, seed=7, prec=H.FP32)
+    ref, _, _ = O.advance(po, Ug, N)
+    base, _, _ = gpu_advance(ph, Ug)
+    for threads, grid in ((128, 1), (256, 3), (352, 0), (96, 8)):
+        ph.block_threads, ph.grid_ctas = threads, grid
+        got, _, _ = gpu_advance(ph, Ug)
+        np.testing.assert_array_equal(got, base)
+    ph.block_threads, ph.grid_ctas = 0, 0
+    # errors are returned, never trapped
+    U_in = torch.zeros((1, 5, 22, 22, 22), dtype=torch.float32, device=dev)
+    U_out = torch.zeros((1, 5, N, N, N), dtype=torch.float32, device=dev)
+    bad = [dict(scheme=7), dict(riemann=9), dict(gamma=1.0), dict(theta=3.0), dict(block_threads=100),
+           dict(block_threads=1024), dict(dx=(0.0, 1.0, 1.0))]
+    for kw in bad:
+        _, p = params_pair(O.CTU, O.PPM, O.ROE, H.FP32, 1e-3, (1 / 32,) * 3)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        with pytest.raises(H.HydroError) as e:
+            H.hydro_advance(p, U_in, U_out)
+        assert e.value.code == H.EINVAL
+    _, p = params_pair(O.VL, O.PPM, O.ROE, H.FP32, 1e-3, (1 / 32,) * 3)  # needs 4 ghost layers
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_advance(p, U_in, U_out, ghost=3)
+    assert e.value.code == H.EGHOST
+    _, p = params_pair(O.CTU, O.PPM, O.ROE, H.FP64, 1e-3, (1 / 32,) * 3)  # FP64 needs its workspace
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_advance(p, U_in.double(), U_out.double())
+    assert e.value.code == H.EWORKSPACE
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_advance(ph, U_in, U_out, N=8, ghost=7)
+    assert e.value.code == H.EUNSUPPORTED
+    torch.cuda.synchronize()
+
+
+def test_plain_method_sod_10_steps_fp64(torch_dev):
+    """Plain-method workload: uniform 32^3 FP64, Sod along x, outflow, MHM +
+    PLM minmod + Roe, 10 steps at CFL 0.5; every step within 1e-12."""
+    torch, dev = torch_dev
+    n, N, g = 32, 16, 2
+    U = W.sod(n, 0)
+    dx = (1.0 / n,) * 3
+    po, ph = params_pair(O.MHM, O.PLM, O.ROE, H.FP64, 0.0, dx)
+    with_workspace(ph, dev)
+    ft = torch.tensor(U, dtype=torch.float64, device=dev)
+    out = torch.empty_like(ft)
+    ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    dtt = torch.zeros(1, dtype=torch.float64, device=dev)
+    ph.dt_dev = dtt
+    orig = W.group_origins(n, n, n, N)
+    for step in range(10):
+        dt = O.cfl_dt(U, dx, 0.5)
+        H.hydro_cfl_dt(ft, dx, 0.5, dtt, ws, precision=H.FP64)
+        po.dt = dt
+        U = W.scatter_groups(O.advance(po, O.gather(U, orig, N, g, bc=1), N)[0], n, n, n)
+        H.hydro_advance_uniform(ph, ft, out, bc=H.BC_OUTFLOW)
+        torch.cuda.synchronize()
+        assert dtt.item() == dt
+        assert rel_l1(out.cpu().numpy()[None], U[None]) <= TOL_FP64, step
+        ft, out = out, ft
+        ft.copy_(torch.tensor(U, device=dev))  # both sides continue from the oracle state
+
+
+@pytest.mark.parametrize("prec", [H.FP32, H.FP64])
+def test_full_size_sampled(torch_dev, prec):
+    """256^3 periodic lognormal box (4096 groups, 3 ghost layers), CTU + PPM +
+    Roe, one step through the fused path as the benchmark runs it; 6 sampled
+    groups compared with the oracle element by element, the box by totals."""
+    torch, dev = torch_dev
+    n, N, g = 256, 16, 3
+    U = quantise(W.lognormal(n, seed=1, mach=1.5), prec)
+    dx = (1.0 / n,) * 3
+    dt = O.cfl_dt(U, dx, 0.4)
+    po, ph = params_pair(O.CTU, O.PPM, O.ROE, prec, dt, dx)
+    with_workspace(ph, dev)
+    ft = torch.tensor(U, dtype=tdtype(prec), device=dev)
+    out = torch.empty_like(ft)
+    st = torch.empty(4096, dtype=torch.int32, device=dev)
+    H.hydro_advance_uniform(ph, ft, out, bc=H.BC_PERIODIC, status=st)
+    got = out.double().cpu().numpy()
+    assert np.all(st.cpu().numpy() & H.ST_ERROR_MASK == 0)
+    rng = np.random.default_rng(0)
+    pick = np.concatenate([[0, 4095], rng.choice(4096, 4, replace=False)])
+    orig = W.group_origins(n, n, n, N)[pick]
+    ref, _, _ = O.advance(po, O.gather(U, orig, N, g, bc=0), N)
+    for k, (x0, y0, z0) in enumerate(orig):
+        sub = got[:, z0:z0 + N, y0:y0 + N, x0:x0 + N]
+        assert rel_l1(sub[None], ref[k][None]) <= (TOL_FP64 if prec == H.FP64 else TOL_FP32)
+    tot0 = U.reshape(5, -1).sum(axis=1)
+    tot1 = got.reshape(5, -1).sum(axis=1)
+    scale = np.abs(U).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(tot1 - tot0) <= (1e-12 if prec == H.FP64 else 1e-5) * scale)
