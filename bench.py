@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the unsplit patch-group fluid update on GB300.
+
+Workload (the paper's uniform-mesh benchmark shape, Sec. 5.1, with synthetic
+data): a 256^3 periodic box of 4096 patch groups (16^3 cells + 3 ghost
+layers), lognormal density (sigma 0.5, k^-3 Gaussian field, seed 1), p = 1,
+k^-3 random velocities at rms Mach 1.5, gamma 1.4, CTU + PPM (minmod) + Roe
+with HLLE fallback, CFL 0.4, FP32.
+
+One step = the whole hot path: ghost gather fused into the CTU group update
+(reconstruct + trace, Riemann, transverse correction, Riemann, update, store
+the group-boundary fluxes), then the FP64 CFL reduction that gives the next
+step's dt on the device.  Metric: cell-updates/s (interior cells x steps /
+device time), p50/p99 step latency, the roofline fraction of the dominant
+kernel, the oracle on the host cores as cpu_baseline, and an end-to-end
+number through host buffers.  FP64 and the mixed form are measured on the same
+box as extra lines of detail.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank advances its own box
+(independent replicas: weak scaling, no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (CTU+PPM+Roe, FP32 vs FP64) and % roofline; p50/p99 step latency"
+UNIT = "cell-updates/s"
+N_BOX = 256
+CFL = 0.4
+FLOORS = dict(dens_floor=1e-6, pres_floor=1e-6)
+CONFIG = {"workload": "uniform 256^3 periodic box as 4096 16^3-cell patch groups (3 ghost layers); lognormal "
+                      "density sigma 0.5 (k^-3 Gaussian field, seed 1), rms Mach 1.5 k^-3 velocities; CTU+PPM+Roe",
+          "scheme": "ctu", "recon": "ppm", "limiter": "minmod", "riemann": "roe", "roe_fallback": "hlle",
+          "box": [256, 256, 256], "patch_group": 16, "ghost": 3, "groups": 4096, "cfl": CFL, "gamma": 1.4,
+          "step": "fused gather + CTU group update + boundary-flux store, then FP64 CFL reduction (device dt)",
+          "l2": "no flush: the 335 MB FP32 state (671 MB FP64) exceeds the 129 MB L2 and is streamed every step"}
+
+
+def sm_peak_fp32_tflops(nsm, sm_mhz):
+    """FP32 ALU peak: SMs x 128 FP32 lanes x 2 flop per FMA x clock."""
+    return nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1103_3373_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.idx = vis.split(",")[local_rank] if vis else str(local_rank)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", self.idx], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power))}
+
+
+def make_params(H, precision, dx):
+    return H.Params(scheme=H.CTU, recon=H.PPM, limiter=H.LIM_MINMOD, riemann=H.RS_ROE, roe_fallback=H.RS_HLLE,
+                    precision=precision, gamma=1.4, dx=dx, **FLOORS)
+
+
+def time_box(box, steps, warmup, torch, sampler=None):
+    """Time `steps` steps (after `warmup`) with CUDA events on the box's stream.
+    Returns per-step ms, mean advance-kernel ms and total ms."""
+    s = box.stream
+    for _ in range(warmup):
+        box.step(s)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    torch.cuda.synchronize()
+    t0.record(s)
+    for k in range(steps):
+        ev[k][0].record(s)
+        box.advance(s)
+        ev[k][1].record(s)
+        box.swap()
+        box.compute_dt(s)
+        ev[k][2].record(s)
+    t1.record(s)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    adv_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    return step_ms, float(np.mean(adv_ms)), t0.elapsed_time(t1), clocks
+
+
+def cpu_baseline(U, dx, budget_s=12.0):
+    """The FP64 oracle as it stands, OpenMP over patch groups on all host cores,
+    on a bounded sample of the workload's groups (one step each)."""
+    import oracle as O
+    from paper_1103_3373_gb300 import workloads as W
+    Uq = U.astype(np.float32).astype(np.float64)
+    dt = O.cfl_dt(Uq, dx, CFL, 1.4, **FLOORS)
+    P = O.Params(scheme=O.CTU, recon=O.PPM, riemann=O.ROE, limiter=O.MINMOD, fallback=O.HLLE, gamma=1.4, dt=dt,
+                 dx=dx, **FLOORS)
+    orig = W.group_origins(N_BOX, N_BOX, N_BOX, 16)
+    cores = O.max_threads()
+    probe = min(len(orig), max(8, cores))
+    Ug = O.gather(Uq, orig[:probe], 16, 3, bc=0)
+    t = time.perf_counter()
+    O.advance(P, Ug, 16)
+    per_group = (time.perf_counter() - t) / probe
+    S = int(min(len(orig), max(probe, budget_s / max(per_group, 1e-6))))
+    S = max(cores, (S // cores) * cores)
+    Ug = O.gather(Uq, orig[:S], 16, 3, bc=0)
+    t = time.perf_counter()
+    O.advance(P, Ug, 16)
+    el = time.perf_counter() - t
+    # one core, small sample
+    S1 = max(1, min(4, S))
+    t = time.perf_counter()
+    O.advance(P, Ug[:S1], 16, nthreads=1)
+    el1 = time.perf_counter() - t
+    return {"value": S * 4096 / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one CTU+PPM+Roe FP64 step of the first %d of the 4096 patch groups of the same box "
+                      "(%.1f s on %d threads)" % (S, el, cores),
+            "single_core": {"value": S1 * 4096 / el1, "groups": S1, "seconds": el1}}
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the oracle (FP64 CPU), as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1103_3373_gb300 import workloads as W
+    U = W.lognormal(N_BOX, seed=1, mach=1.5)
+    dx = (1.0 / N_BOX,) * 3
+    Uq = U.astype(np.float32).astype(np.float64)
+    dt = O.cfl_dt(Uq, dx, CFL, 1.4, **FLOORS)
+    P = O.Params(scheme=O.CTU, recon=O.PPM, riemann=O.ROE, limiter=O.MINMOD, fallback=O.HLLE, gamma=1.4, dt=dt,
+                 dx=dx, **FLOORS)
+    orig = W.group_origins(N_BOX, N_BOX, N_BOX, 16)
+    cores = O.max_threads()
+    probe = O.gather(Uq, orig[:cores], 16, 3, bc=0)
+    t = time.perf_counter()
+    O.advance(P, probe, 16)
+    per_group = (time.perf_counter() - t) / cores
+    budget = min(10.0, 150.0 / max(1, args.steps + args.warmup))  # whole run within a few minutes
+    S = int(max(cores, min(len(orig), budget / max(per_group, 1e-6))))
+    S = max(cores, (S // cores) * cores)
+    Ug = O.gather(Uq, orig[:S], 16, 3, bc=0)
+    for _ in range(args.warmup):
+        O.advance(P, Ug, 16)
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.advance(P, Ug, 16)
+        ts.append(time.perf_counter() - t)
+    el = sum(ts)
+    value = S * 4096 * args.steps / el
+    sample = "each step: one CTU+PPM+Roe FP64 oracle step of the first %d of the 4096 patch groups" % S
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mixed / VL detail lines")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--quick", action="store_true", help="main line only (no extra, cpu_baseline or e2e legs)")
+    args = ap.parse_args()
+    if args.quick:
+        args.no_extra = args.no_cpu = True
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    from paper_1103_3373_gb300 import build as hb
+    if rank == 0 and world == 1:
+        hb.build()
+    from paper_1103_3373_gb300 import hydro as H
+    from paper_1103_3373_gb300 import runtime as RT
+    from paper_1103_3373_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    U = W.lognormal(N_BOX, seed=1, mach=1.5)
+    dx = (1.0 / N_BOX,) * 3
+    cells = N_BOX ** 3
+    stream = torch.cuda.Stream(device=dev)
+    box = RT.UniformBox(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev, stream=stream)
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, adv_ms, total_ms, clocks = time_box(box, args.steps, args.warmup, torch, sampler)
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = box.status.cpu().numpy()
+    finite = bool(torch.isfinite(box.state()).all().item())
+    value = world * cells * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the fused CTU group update)
+    with open(os.path.join(ROOT, "paper_1103_3373_gb300", "data", "flops_per_cell.json")) as fh:
+        flops_cell = json.load(fh)["entries"]["ctu-ppm-roe"]["flops"]
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sm_peak_fp32_tflops(props.multi_processor_count, sm_max)
+    achieved = flops_cell * cells / (adv_ms / 1e3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "paper_1103_3373_gb300", "data", "ncu_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            tj = json.load(fh)
+        if tj.get("source_sha") == source_hash():
+            traffic = tj["bytes_per_cell"] * cells
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "advance_kernel<CTU,PPM,ROE,FP32,16> (fused gather)",
+                "flops_per_cell": flops_cell, "kernel_ms": adv_ms,
+                "peak_note": "derived, not measured: %d SMs x 128 FP32 lanes x 2 flop/FMA x %.0f MHz"
+                             % (props.multi_processor_count, sm_max),
+                "hbm_frac_of_measured": (40.0 * cells + 30.0 * 4 * 256 * 4096) / (adv_ms / 1e3) / 1e9 /
+                                        peaks.get("hbm_gbs", 6775.3)}
+
+    # end to end through host buffers (pinned), same metric
+    e2e = None
+    if not args.quick:
+        hs = RT.HostBoxStepper(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev)
+        ke = max(5, min(args.steps, 50))
+        for _ in range(3):
+            hs.step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(ke):
+            hs.step()
+        b.record()
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b)
+        e2e = {"value": world * cells * ke / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": hs.h2d_bytes,
+               "d2h_bytes_per_step": hs.d2h_bytes, "steps": ke, "ms_per_step": e_ms / ke}
+        del hs
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        del box
+        torch.cuda.empty_cache()
+        for name, prec, k in (("fp64", H.FP64, 4), ("mixed", H.FP32_MIXED, 50)):
+            bx = RT.UniformBox(U, make_params(H, prec, dx), cfl=CFL, device=dev, stream=stream)
+            sm, am, tm, _ = time_box(bx, k, 3, torch)
+            extra[name] = {"value": cells * k / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / k,
+                           "kernel_ms": am, "steps": k}
+            del bx
+            torch.cuda.empty_cache()
+        p = make_params(H, H.FP32, dx)
+        p.scheme, p.recon, p.riemann = H.VL, H.PLM, H.RS_HLLC
+        bx = RT.UniformBox(U, p, cfl=CFL, device=dev, stream=stream)
+        sm, am, tm, _ = time_box(bx, 50, 3, torch)
+        extra["vl_plm_hllc_fp32"] = {"value": cells * 50 / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / 50,
+                                     "kernel_ms": am}
+        del bx
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(U, dx)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(CONFIG, parallelism="replicas%d" % world if world > 1 else "single GPU"),
+                "p50_step_ms": RT.percentile(step_ms, 50), "p99_step_ms": RT.percentile(step_ms, 99),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 3 * args.steps, "status_error_groups": int(np.count_nonzero(st & H.ST_ERROR_MASK)),
+                "state_finite": finite, "extra": extra,
+                "paper_context": "3.0e7 cell-updates/s, CTU+PPM+Roe FP32 on one Tesla C2050 incl. transfers "
+                                 "(Sec. 3.2); other hardware, not a target"}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -41,9 +41,17 @@ struct OpTally {
 extern thread_local OpTally g_tally;
 extern thread_local int g_section;
 
+// Operations are attributed to the outermost open section (a Riemann solve
+// owns the state conversions it makes), and a call is counted only when its
+// section is entered from outside any other section.
 struct SectionScope {
   int saved;
-  explicit SectionScope(int s) : saved(g_section) { g_section = s; g_tally.calls[s]++; }
+  explicit SectionScope(int s) : saved(g_section) {
+    if (g_section == SEC_OTHER) {
+      g_section = s;
+      g_tally.calls[s]++;
+    }
+  }
   ~SectionScope() { g_section = saved; }
 };
 

@@ -3,28 +3,28 @@
 //
 // The paper's GPU solver keeps whole-group face values and fluxes in global
 // memory (Sec. 3.1).  Here each CTA walks its group along z and keeps only the
-// planes still needed in small ring buffers (shared memory for FP32, a
-// per-CTA slice of an L2-resident workspace for FP64).  At iteration t the CTA
-//   A  loads plane pA = t-1-S and converts it to primitives        (W ring)
-//   B  reconstructs + traces the cells of plane pB = pA-S to t+dt/2 in all
-//      three directions (step (1))                         (face-state rings)
-//   C  solves the stage-1 Riemann problems on the x/y faces of plane pB and
-//      the z faces between pB-1 and pB (step (2))            (flux rings)
-//   D  applies the transverse flux-gradient correction to the face states of
-//      plane pD = pB-1 (step (3))
-//   E  solves the stage-2 Riemann problems of plane pD (x/y) and of the z faces
-//      below it, storing group-boundary fluxes at once (steps (3) and (5))
-//   F  updates plane pD-1 (step (4)); it runs at the start of the next
-//      iteration, in the same barrier interval as that iteration's A (the two
-//      touch disjoint buffers)
-// with S the reconstruction stencil (1 PLM, 2 PPM).  Every stage is a flat
-// loop of the CTA's threads over the plane's work items (Sec. 3.1's
-// index-flattening), separated by block barriers.
+// planes still needed in ring buffers (shared memory for FP32, a per-CTA
+// slice of an L2-resident workspace for FP64).  Iteration t works on three
+// planes, q = t-1 (tracing), q-1 (final fluxes) and q-3 (update), in three
+// barrier intervals:
+//   S1  B: reconstruct + trace the cells of plane q to t+dt/2 in all three
+//          directions (step (1));
+//       F: conservative update of plane q-3 (step (4));
+//   S2  C: stage-1 Riemann problems on the x/y faces of plane q and the z
+//          faces between q-1 and q (step (2));
+//   S3  E: stage-2 Riemann problems of plane q-1 (x/y faces) and of the z
+//          faces below it; each face first applies the transverse
+//          flux-gradient correction (step (3)) to its two states, and fluxes
+//          on the group boundary are stored at once (step (5));
+//       A: load of the next input plane (primitives).
+// Every corrected state feeds exactly one face, so correcting inside the face
+// item recomputes nothing.  The stages are flat loops of the CTA's threads
+// over the plane's work items (Sec. 3.1's index flattening).
 //
-// Index ranges (interior coordinates, cells 0..N-1):
-//   traced states on cells [-1,N]^3; stage-1 fluxes on the faces of those
-//   cells; corrected states on cells [-1,N] along their normal and [0,N-1]
-//   laterally; stage-2 fluxes on the faces of the interior cells.
+// Index ranges (interior coordinates, cells 0..N-1): traced states on the
+// cells [-1,N]^3; stage-1 fluxes on the faces of those cells; corrected
+// states on the cells [-1,N] along their normal and [0,N-1] laterally;
+// stage-2 fluxes on the faces of the interior cells.
 #pragma once
 #include "stages.cuh"
 
@@ -40,9 +40,10 @@ template <int N, int S> struct CtuLayout {
   static constexpr int F1X = 5 * L * (N + 1);  // [var][L rows][N+1 faces]
   static constexpr int F1XYPL = 2 * F1X;       // x then y ([var][N+1 faces][L cols])
   static constexpr int F1ZPL = 5 * LL;
+  static constexpr int D1XY = 3;               // stage-1 x/y flux planes kept
   static constexpr int OFF_FR = WR::ELEMS;
   static constexpr int OFF_F1XY = OFF_FR + FRf::ELEMS;
-  static constexpr int OFF_F1Z = OFF_F1XY + 2 * F1XYPL;
+  static constexpr int OFF_F1Z = OFF_F1XY + D1XY * F1XYPL;
   static constexpr int TOTAL = OFF_F1Z + 2 * F1ZPL;
 };
 
@@ -51,19 +52,64 @@ template <class T, int N, int S> struct CtuF1 {
   T* base;
   // stage-1 x flux: face f (between cells f-1 and f), row jj
   __device__ __forceinline__ T& x(int p, int v, int jj, int f) const {
-    return base[slot<2>(p) * Lay::F1XYPL + (v * Lay::L + jj) * (N + 1) + f];
+    return base[slot<Lay::D1XY>(p) * Lay::F1XYPL + (v * Lay::L + jj) * (N + 1) + f];
   }
   __device__ __forceinline__ T& y(int p, int v, int f, int ii) const {
-    return base[slot<2>(p) * Lay::F1XYPL + Lay::F1X + (v * (N + 1) + f) * Lay::L + ii];
+    return base[slot<Lay::D1XY>(p) * Lay::F1XYPL + Lay::F1X + (v * (N + 1) + f) * Lay::L + ii];
   }
   // stage-1 z flux of the face below plane p
   __device__ __forceinline__ T& z(int p, int v, int jj, int ii) const {
-    return base[2 * Lay::F1XYPL + slot<2>(p) * Lay::F1ZPL + (v * Lay::L + jj) * Lay::L + ii];
+    return base[Lay::D1XY * Lay::F1XYPL + slot<2>(p) * Lay::F1ZPL + (v * Lay::L + jj) * Lay::L + ii];
   }
 };
 
-template <class T, class S, bool MIXED, int RS, int REC, int N>
-__device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
+// Step (1) for one cell along direction D: reconstruction of the primitive
+// ring around (jj, ii) of plane p, characteristic tracing to t + dt/2, and the
+// two traced face states as conserved variables (Ul: left face, Ur: right).
+template <int D, int REC, int LIM, class T, class WRing>
+__device__ __forceinline__ void trace_cell(const WRing& Wr, int p, int jj, int ii, const Opts<T>& o, T dtdx, T Ul[5],
+                                           T Ur[5]) {
+  constexpr int S_ = REC == PPM ? 2 : 1;
+  T w[5][5], WLf[5], WRf[5], dW[5], W0[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+#pragma unroll
+    for (int o2 = -S_; o2 <= S_; ++o2) {
+      if (D == 0) w[v][o2 + 2] = Wr(p, v, jj + S_, ii + S_ + o2);
+      else if (D == 1) w[v][o2 + 2] = Wr(p, v, jj + S_ + o2, ii + S_);
+      else w[v][o2 + 2] = Wr(p + o2, v, jj + S_, ii + S_);
+    }
+    W0[v] = w[v][2];
+  }
+  recon5<REC, LIM>(w, o, WLf, WRf, dW);
+  T w0l[5], a[5], b[5], tl[5], tr[5];
+  rot_in<D>(W0, w0l);
+  if (REC == PPM) {
+    rot_in<D>(WLf, a);
+    rot_in<D>(WRf, b);
+    trace_ppm(w0l, a, b, dtdx, o.gas, tl, tr);
+  } else {
+    rot_in<D>(dW, a);
+    trace_plm(w0l, a, dtdx, o.gas, tl, tr);
+  }
+  T wg[5];
+  rot_out<D>(tl, wg);
+  cons(wg, Ul, o.gas);
+  rot_out<D>(tr, wg);
+  cons(wg, Ur, o.gas);
+}
+
+// Transverse flux-gradient correction (step (3)) of one face state:
+//   u = (u - h1 (G1+ - G1-)) - h2 (G2+ - G2-), the two other directions in
+//   increasing order.
+template <class T> __device__ __forceinline__ T correct(T u, T h1, T a1p, T a1m, T h2, T a2p, T a2m) {
+  u = u - h1 * (a1p - a1m);
+  u = u - h2 * (a2p - a2m);
+  return u;
+}
+
+template <class T, class S, bool MIXED, int RS, int REC, int LIM, int N>
+__device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = CtuLayout<N, S_>;
   constexpr int L = Lay::L, LL = Lay::LL, LW = Lay::LW;
@@ -72,76 +118,79 @@ __device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
   CtuF1<T, N, S_> F1{ring + Lay::OFF_F1XY};
   const int nthr = blockDim.x;
   const int tid = threadIdx.x;
+  const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
   unsigned st = 0;
 
-  // one extra iteration drains the last update
-  constexpr int T_ITERS = N + 4 + 2 * S_;
+  // prologue: the planes the first tracing needs
+  for (int p = -1 - S_; p <= -1 + S_; ++p) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, p, 1 + S_, Wr);
+  __syncthreads();
+
+  constexpr int T_ITERS = N + 4;
   for (int t = 0; t < T_ITERS; ++t) {
-    const int pA = t - 1 - S_;
-    const int pB = pA - S_;
-    const int pD = pB - 1;
-    const int pF = pD - 2;  // the plane whose final fluxes the previous iteration completed
-
-    // ---- F (update of plane pF) and A (load of plane pA) ----------------
-    if (pF >= 0 && pF < N) st |= stage_update<T, S, MIXED, N>(C, o, R, pF);
-    if (pA <= N + S_) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, pA, 1 + S_, Wr);
-    __syncthreads();
-
-    // ---- B: reconstruction + characteristic tracing of plane pB ---------
-    if (pB >= -1 && pB <= N) {
-      for (int idx = tid; idx < 3 * LL; idx += nthr) {
-        int d = idx / LL;
-        int rem = idx - d * LL;
-        int jj = rem / L, ii = rem - jj * L;
-        T w[5][5], WLf[5], WRf[5], dW[5], W0[5];
+    const int q = t - 1;  // plane traced and given stage-1 fluxes
+    const int r = q - 1;  // plane given stage-2 fluxes
+    const int u = q - 3;  // plane updated
+    // ---- S1: B (trace plane q) and F (update plane u) --------------------
+    {
+      // the update's reads of U^n are issued first and consumed after the
+      // tracing, so their latency hides behind it
+      const int nf = (u >= 0 && u < N) ? N * N : 0;
+      T Un0[5];
+      const bool pre_f = tid < nf;
+      if (pre_f) {
+        int j = tid / N, i = tid - j * N;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Un0[v] = (T)C.load_raw(v, i, j, u);
+      }
+      if (q <= N) {
+        for (int k = tid; k < 3 * LL; k += nthr) {
+          int d = k / LL;
+          int rem = k - d * LL;
+          int jj = rem / L, ii = rem - jj * L;
+          T Ul[5], Ur[5];
+          if (d == 0) {
+            trace_cell<0, REC, LIM>(Wr, q, jj, ii, o, C.dtdx[0], Ul, Ur);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              R.XY(q, 0, 0, v, jj, ii) = Ul[v];
+              R.XY(q, 0, 1, v, jj, ii) = Ur[v];
+            }
+          } else if (d == 1) {
+            trace_cell<1, REC, LIM>(Wr, q, jj, ii, o, C.dtdx[1], Ul, Ur);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              R.XY(q, 1, 0, v, jj, ii) = Ul[v];
+              R.XY(q, 1, 1, v, jj, ii) = Ur[v];
+            }
+          } else {
+            trace_cell<2, REC, LIM>(Wr, q, jj, ii, o, C.dtdx[2], Ul, Ur);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              R.Zs(q, 0, v, jj, ii) = Ul[v];
+              R.Zs(q, 1, v, jj, ii) = Ur[v];
+            }
+          }
+        }
+      }
+      for (int k = tid; k < nf; k += nthr) {
+        int j = k / N, i = k - j * N;
+        T Uc[5], dF[3][5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-#pragma unroll
-          for (int o2 = -S_; o2 <= S_; ++o2) {
-            if (d == 0) w[v][o2 + 2] = Wr(pB, v, jj + S_, ii + S_ + o2);
-            else if (d == 1) w[v][o2 + 2] = Wr(pB, v, jj + S_ + o2, ii + S_);
-            else w[v][o2 + 2] = Wr(pB + o2, v, jj + S_, ii + S_);
-          }
-          W0[v] = w[v][2];
+          Uc[v] = k == tid ? Un0[v] : (T)C.load_raw(v, i, j, u);
+          dF[0][v] = R.F2x(u, v, j, i + 1) - R.F2x(u, v, j, i);
+          dF[1][v] = R.F2y(u, v, j + 1, i) - R.F2y(u, v, j, i);
+          dF[2][v] = R.F2z(u + 1, v, j, i) - R.F2z(u, v, j, i);
         }
-        recon5<REC>(w, o, WLf, WRf, dW);
-        T w0l[5], a[5], b[5], tl[5], tr[5];
-        rot_in(W0, w0l, d);
-        if (REC == PPM) {
-          rot_in(WLf, a, d);
-          rot_in(WRf, b, d);
-          trace_ppm(w0l, a, b, C.dtdx[d], o.gas, tl, tr);
-        } else {
-          rot_in(dW, a, d);
-          trace_plm(w0l, a, C.dtdx[d], o.gas, tl, tr);
-        }
-        T wg[5], U[5];
-        rot_out(tl, wg, d);
-        cons(wg, U, o.gas);
-        if (d < 2) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) R.XY(pB, d, 0, v, jj, ii) = U[v];
-        } else {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) R.Zs(pB, 0, v, jj, ii) = U[v];
-        }
-        rot_out(tr, wg, d);
-        cons(wg, U, o.gas);
-        if (d < 2) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) R.XY(pB, d, 1, v, jj, ii) = U[v];
-        } else {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) R.Zs(pB, 1, v, jj, ii) = U[v];
-        }
+        st |= update_cell_from<T, S, MIXED, N>(C, i, j, u, Uc, dF, o.gas);
       }
     }
     __syncthreads();
 
-    // ---- C: stage-1 fluxes (x/y faces of plane pB, z faces below it) ----
-    if (pB >= -1 && pB <= N) {
+    // ---- S2: C, stage-1 fluxes (x/y faces of plane q, z faces below it) --
+    if (q <= N) {
       constexpr int NX = L * (N + 1);
-      const int nz = pB >= 0 ? LL : 0;
+      const int nz = q >= 0 ? LL : 0;
       const int cnt = 2 * NX + nz;
       for (int idx = tid; idx < cnt; idx += nthr) {
         T UL[5], UR[5], F[5];
@@ -149,102 +198,135 @@ __device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
           int jj = idx / (N + 1), f = idx - jj * (N + 1);
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            UL[v] = R.XY(pB, 0, 1, v, jj, f);
-            UR[v] = R.XY(pB, 0, 0, v, jj, f + 1);
+            UL[v] = R.XY(q, 0, 1, v, jj, f);
+            UR[v] = R.XY(q, 0, 0, v, jj, f + 1);
           }
-          st |= riemann<T, MIXED, RS>(0, UL, UR, o, F);
+          st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) F1.x(pB, v, jj, f) = F[v];
+          for (int v = 0; v < 5; ++v) F1.x(q, v, jj, f) = F[v];
         } else if (idx < 2 * NX) {
           int k = idx - NX;
           int f = k / L, ii = k - f * L;
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            UL[v] = R.XY(pB, 1, 1, v, f, ii);
-            UR[v] = R.XY(pB, 1, 0, v, f + 1, ii);
+            UL[v] = R.XY(q, 1, 1, v, f, ii);
+            UR[v] = R.XY(q, 1, 0, v, f + 1, ii);
           }
-          st |= riemann<T, MIXED, RS>(1, UL, UR, o, F);
+          st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) F1.y(pB, v, f, ii) = F[v];
+          for (int v = 0; v < 5; ++v) F1.y(q, v, f, ii) = F[v];
         } else {
           int k = idx - 2 * NX;
           int jj = k / L, ii = k - jj * L;
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            UL[v] = R.Zs(pB - 1, 1, v, jj, ii);
-            UR[v] = R.Zs(pB, 0, v, jj, ii);
+            UL[v] = R.Zs(q - 1, 1, v, jj, ii);
+            UR[v] = R.Zs(q, 0, v, jj, ii);
           }
-          st |= riemann<T, MIXED, RS>(2, UL, UR, o, F);
+          st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) F1.z(pB, v, jj, ii) = F[v];
+          for (int v = 0; v < 5; ++v) F1.z(q, v, jj, ii) = F[v];
         }
       }
     }
     __syncthreads();
 
-    // ---- D: transverse flux-gradient correction of plane pD -------------
-    //   U -= dt/(2 dx_e) (F1_e(+1/2) - F1_e(-1/2)) for the two e != d, in
-    //   increasing e
-    if (pD >= -1 && pD <= N) {
-      const bool xy = pD >= 0 && pD < N;
-      const int nx = xy ? L * N : 0;  // x states: rows j in [0,N), cells ii in [0,L)
-      const int cnt = 2 * nx + N * N;
-      const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
-      for (int idx = tid; idx < cnt; idx += nthr) {
+    // ---- S3: E, corrected stage-2 fluxes of plane r; A, next input plane --
+    {
+      const int nx = (r >= 0 && r < N) ? N * (N + 1) : 0;
+      const int nz = (r >= 0 && r <= N) ? N * N : 0;
+      const int ne = 2 * nx + nz;
+      const int pa = q + 1 + S_;  // plane the next tracing needs last
+      const int na = (pa <= N + S_) ? LW * LW : 0;
+      // the next plane's global loads are issued first and converted after
+      // the Riemann work, so their latency hides behind it
+      T Ua0[5];
+      if (tid < na) {
+        int jj = tid / LW, ii = tid - jj * LW;
+        C.load5(ii - 1 - S_, jj - 1 - S_, pa, Ua0);
+      }
+      for (int idx = tid; idx < ne; idx += nthr) {
+        T UL[5], UR[5], F[5];
         if (idx < nx) {
-          int j = idx / L, ii = idx - j * L, jj = j + 1;
+          // x face f of row j: R state of cell f-1 and L state of cell f
+          int j = idx / (N + 1), f = idx - j * (N + 1), jj = j + 1;
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            T gy = F1.y(pD, v, jj, ii) - F1.y(pD, v, jj - 1, ii);
-            T gz = F1.z(pD + 1, v, jj, ii) - F1.z(pD, v, jj, ii);
+            UL[v] = correct(R.XY(r, 0, 1, v, jj, f), h1, F1.y(r, v, jj, f), F1.y(r, v, jj - 1, f), h2,
+                            F1.z(r + 1, v, jj, f), F1.z(r, v, jj, f));
+            UR[v] = correct(R.XY(r, 0, 0, v, jj, f + 1), h1, F1.y(r, v, jj, f + 1), F1.y(r, v, jj - 1, f + 1), h2,
+                            F1.z(r + 1, v, jj, f + 1), F1.z(r, v, jj, f + 1));
+          }
+          st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-              T u = R.XY(pD, 0, side, v, jj, ii);
-              u = u - h1 * gy;
-              u = u - h2 * gz;
-              R.XY(pD, 0, side, v, jj, ii) = u;
-            }
+          for (int v = 0; v < 5; ++v) R.F2x(r, v, j, f) = F[v];
+          if (f == 0 || f == N) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 0 : 1, v, r, j, F[v]);
           }
         } else if (idx < 2 * nx) {
+          // y face f of column i: R state of cell f-1 and L state of cell f
           int k = idx - nx;
-          int jj = k / N, i = k - jj * N, ii = i + 1;
+          int f = k / N, i = k - f * N, ii = i + 1;
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            T gx = F1.x(pD, v, jj, ii) - F1.x(pD, v, jj, ii - 1);
-            T gz = F1.z(pD + 1, v, jj, ii) - F1.z(pD, v, jj, ii);
+            UL[v] = correct(R.XY(r, 1, 1, v, f, ii), h0, F1.x(r, v, f, ii), F1.x(r, v, f, ii - 1), h2,
+                            F1.z(r + 1, v, f, ii), F1.z(r, v, f, ii));
+            UR[v] = correct(R.XY(r, 1, 0, v, f + 1, ii), h0, F1.x(r, v, f + 1, ii), F1.x(r, v, f + 1, ii - 1), h2,
+                            F1.z(r + 1, v, f + 1, ii), F1.z(r, v, f + 1, ii));
+          }
+          st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-              T u = R.XY(pD, 1, side, v, jj, ii);
-              u = u - h0 * gx;
-              u = u - h2 * gz;
-              R.XY(pD, 1, side, v, jj, ii) = u;
-            }
+          for (int v = 0; v < 5; ++v) R.F2y(r, v, f, i) = F[v];
+          if (f == 0 || f == N) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 2 : 3, v, r, i, F[v]);
           }
         } else {
+          // z face below plane r: R state of plane r-1 and L state of plane r
           int k = idx - 2 * nx;
           int j = k / N, i = k - j * N, jj = j + 1, ii = i + 1;
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            T gx = F1.x(pD, v, jj, ii) - F1.x(pD, v, jj, ii - 1);
-            T gy = F1.y(pD, v, jj, ii) - F1.y(pD, v, jj - 1, ii);
+            UL[v] = correct(R.Zs(r - 1, 1, v, jj, ii), h0, F1.x(r - 1, v, jj, ii), F1.x(r - 1, v, jj, ii - 1), h1,
+                            F1.y(r - 1, v, jj, ii), F1.y(r - 1, v, jj - 1, ii));
+            UR[v] = correct(R.Zs(r, 0, v, jj, ii), h0, F1.x(r, v, jj, ii), F1.x(r, v, jj, ii - 1), h1,
+                            F1.y(r, v, jj, ii), F1.y(r, v, jj - 1, ii));
+          }
+          st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-              T u = R.Zs(pD, side, v, jj, ii);
-              u = u - h0 * gx;
-              u = u - h1 * gy;
-              R.Zs(pD, side, v, jj, ii) = u;
-            }
+          for (int v = 0; v < 5; ++v) R.F2z(r, v, j, i) = F[v];
+          if (r == 0 || r == N) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) C.store_flux(r == 0 ? 4 : 5, v, j, i, F[v]);
           }
         }
       }
+      for (int k = tid; k < na; k += nthr) {
+        int jj = k / LW, ii = k - jj * LW;
+        T U[5], W[5];
+        if (k == tid) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) U[v] = Ua0[v];
+        } else {
+          C.load5(ii - 1 - S_, jj - 1 - S_, pa, U);
+        }
+        prim<T, MIXED>(U, W, o.gas);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Wr(pa, v, jj, ii) = W[v];
+      }
     }
-    __syncthreads();
-
-    // ---- E: stage-2 fluxes of plane pD, group-boundary fluxes (step 5) --
-    if (pD >= 0 && pD <= N) st |= stage_flux2<T, S, MIXED, RS, N>(C, o, R, pD);
     __syncthreads();
   }
   if (st) atomicOr(&st_sh, st);
+}
+
+template <class T, class S, bool MIXED, int RS, int REC, int N>
+__device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
+  if (o.limiter == LIM_MINMOD)
+    ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD, N>(C, o, ring, st_sh);
+  else
+    ctu_group_impl<T, S, MIXED, RS, REC, -1, N>(C, o, ring, st_sh);
 }
 
 }  // namespace hyd

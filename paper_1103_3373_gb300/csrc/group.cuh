@@ -46,16 +46,17 @@ template <class T, class S, int N> struct GroupCtx {
   T dtdx[3], hdtdx[3];
   double dtdx_d[3];
 
-  __device__ __forceinline__ void init(const SegDesc& sg, int gi, const KConst& kc) {
+  // sc[0..2] = dt/dx_d, sc[3..5] = (0.5 dt)/dx_d, evaluated once per group
+  // (group_consts) and shared by the CTA.
+  __device__ __forceinline__ void init(const SegDesc& sg, int gi, const KConst& kc, const double* sc) {
     mode = sg.mode;
     g = kc.ghost;
     M = N + 2 * g;
     Mpl = (long long)M * M;
-    double dt = sg.dt_dev ? *sg.dt_dev : sg.dt;
     for (int d = 0; d < 3; ++d) {
-      dtdx_d[d] = dt / sg.dx[d];
-      dtdx[d] = (T)dtdx_d[d];
-      hdtdx[d] = (T)(0.5 * dt / sg.dx[d]);
+      dtdx_d[d] = sc[d];
+      dtdx[d] = (T)sc[d];
+      hdtdx[d] = (T)sc[3 + d];
     }
     flux = sg.flux ? (S*)sg.flux + (long long)gi * 30 * N * N : nullptr;
     if (mode == 0) {
@@ -79,10 +80,12 @@ template <class T, class S, int N> struct GroupCtx {
     }
   }
 
+  // Box-edge index map for -n <= a < 2n (ghost width <= box size): periodic
+  // wrap or outflow clamp.
   __device__ __forceinline__ static int wrap(int a, int n, int bc) {
     if (bc == 0) {
-      a = a % n;
-      return a < 0 ? a + n : a;
+      a = a < 0 ? a + n : a;
+      return a >= n ? a - n : a;
     }
     return a < 0 ? 0 : (a >= n ? n - 1 : a);
   }
@@ -93,6 +96,19 @@ template <class T, class S, int N> struct GroupCtx {
     if (mode == 0) return (T)in[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
     int sx = wrap(ox + x, X, bc), sy = wrap(oy + y, Y, bc), sz = wrap(oz + z, Z, bc);
     return (T)in[v * XYZ + ((long long)sz * Y + sy) * X + sx];
+  }
+  // All five variables at (x, y, z) (ghost zone allowed).
+  __device__ __forceinline__ void load5(int x, int y, int z, T U[5]) const {
+    if (mode == 0) {
+      const S* p = in + ((long long)(z + g) * M + (y + g)) * M + (x + g);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = (T)p[v * Mpl * M];
+    } else {
+      int sx = wrap(ox + x, X, bc), sy = wrap(oy + y, Y, bc), sz = wrap(oz + z, Z, bc);
+      const S* p = in + ((long long)sz * Y + sy) * X + sx;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = (T)p[v * XYZ];
+    }
   }
   __device__ __forceinline__ S load_raw(int v, int x, int y, int z) const {
     if (mode == 0) return in[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
@@ -110,6 +126,15 @@ template <class T, class S, int N> struct GroupCtx {
   }
 };
 
+// Step constants of one group, computed by one thread.
+__device__ __forceinline__ void group_consts(const SegDesc& sg, double* sc) {
+  double dt = sg.dt_dev ? *sg.dt_dev : sg.dt;
+  for (int d = 0; d < 3; ++d) {
+    sc[d] = dt / sg.dx[d];
+    sc[3 + d] = 0.5 * dt / sg.dx[d];
+  }
+}
+
 // Slot of plane p in a ring of R planes (p >= -8).
 template <int R> __device__ __forceinline__ int slot(int p) { return (p + 8 * R) % R; }
 
@@ -117,21 +142,29 @@ template <int R> __device__ __forceinline__ int slot(int p) { return (p + 8 * R)
 // differences dF[d][v] = F(c + e_d/2) - F(c - e_d/2):
 //   U_new = U - ((dtdx0 dF0 + dtdx1 dF1) + dtdx2 dF2),
 // in FP64 for the mixed form; sets the status bits of the new state.
+template <class T> __device__ __forceinline__ unsigned state_status(const T Un[5], const Gas<T>& gas);
+
+// U0 holds U^n of the cell (already read from the input).
 template <class T, class S, bool MIXED, int N>
-__device__ __forceinline__ unsigned update_cell(const GroupCtx<T, S, N>& C, int x, int y, int z, const T dF[3][5],
-                                                const Gas<T>& gas) {
+__device__ __forceinline__ unsigned update_cell_from(const GroupCtx<T, S, N>& C, int x, int y, int z, const T U0[5],
+                                                     const T dF[3][5], const Gas<T>& gas) {
   T Un[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     if (MIXED) {
       double dU = C.dtdx_d[0] * (double)dF[0][v] + C.dtdx_d[1] * (double)dF[1][v] + C.dtdx_d[2] * (double)dF[2][v];
-      Un[v] = (T)((double)C.load_raw(v, x, y, z) - dU);
+      Un[v] = (T)((double)U0[v] - dU);
     } else {
       T dU = C.dtdx[0] * dF[0][v] + C.dtdx[1] * dF[1][v] + C.dtdx[2] * dF[2][v];
-      Un[v] = (T)C.load_raw(v, x, y, z) - dU;
+      Un[v] = U0[v] - dU;
     }
     C.store(v, x, y, z, (S)Un[v]);
   }
+  return state_status(Un, gas);
+}
+
+// Status bits of an updated state: NaN, density <= 0, pressure <= 0.
+template <class T> __device__ __forceinline__ unsigned state_status(const T Un[5], const Gas<T>& gas) {
   unsigned st = 0;
   bool nan = false;
 #pragma unroll
@@ -144,6 +177,15 @@ __device__ __forceinline__ unsigned update_cell(const GroupCtx<T, S, N>& C, int 
     if (!(p > T(0))) st |= ST_NEG_PRES;
   }
   return st;
+}
+
+template <class T, class S, bool MIXED, int N>
+__device__ __forceinline__ unsigned update_cell(const GroupCtx<T, S, N>& C, int x, int y, int z, const T dF[3][5],
+                                                const Gas<T>& gas) {
+  T U0[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) U0[v] = (T)C.load_raw(v, x, y, z);
+  return update_cell_from<T, S, MIXED, N>(C, x, y, z, U0, dF, gas);
 }
 
 }  // namespace hyd

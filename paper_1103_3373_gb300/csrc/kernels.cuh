@@ -18,11 +18,17 @@ template <int SCH, int REC, int PR, int N> struct KTraits {
                               : SCH == MHM ? MhmLayout<N, S_>::TOTAL
                                            : VlLayout<N, S_>::TOTAL;
   static constexpr bool SMEM = PR != P_FP64;  // FP64 rings do not fit in shared memory
-  static constexpr int MAXT = PR == P_FP64 ? 256 : 384;
+};
+
+// Largest CTA: FP64 kernels need up to 255 registers per thread; the FP32
+// kernels run 16 warps per SM (128 registers per thread) except the exact
+// solver, whose Newton iteration needs more registers.
+template <int PR, int RS> struct MaxThreads {
+  static constexpr int value = PR == P_FP64 ? 256 : (RS == RS_EXACT ? 384 : 512);
 };
 
 template <int SCH, int REC, int RS, int PR, int N>
-__global__ void __launch_bounds__(KTraits<SCH, REC, PR, N>::MAXT, 1)
+__global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
     advance_kernel(const __grid_constant__ WorkTable wt, const KConst kc, void* ws) {
   using Tr = KTraits<SCH, REC, PR, N>;
   using T = typename Tr::T;
@@ -30,6 +36,7 @@ __global__ void __launch_bounds__(KTraits<SCH, REC, PR, N>::MAXT, 1)
   constexpr bool MIXED = Tr::P::MIXED;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned st_sh;
+  __shared__ double sc[6];
   T* ring;
   if constexpr (Tr::SMEM)
     ring = reinterpret_cast<T*>(smem_raw);
@@ -49,9 +56,10 @@ __global__ void __launch_bounds__(KTraits<SCH, REC, PR, N>::MAXT, 1)
     while (s + 1 < wt.nseg && w >= wt.seg[s + 1].first) ++s;
     const SegDesc& sg = wt.seg[s];
     const int gi = w - sg.first;
-    GroupCtx<T, S, N> C;
-    C.init(sg, gi, kc);
+    if (threadIdx.x == 0) group_consts(sg, sc);
     __syncthreads();
+    GroupCtx<T, S, N> C;
+    C.init(sg, gi, kc, sc);
     if constexpr (SCH == CTU)
       ctu_group<T, S, MIXED, RS, REC, N>(C, o, ring, st_sh);
     else if constexpr (SCH == MHM)
@@ -84,7 +92,7 @@ template <int SCH, int REC, int RS, int PR, int N> inline void put_kernel(Kernel
   e.fn = (const void*)&advance_kernel<SCH, REC, RS, PR, N>;
   e.ring_elems = Tr::RING;
   e.elem_bytes = (int)sizeof(typename Tr::T);
-  e.max_threads = Tr::MAXT;
+  e.max_threads = MaxThreads<PR, RS>::value;
   e.smem = Tr::SMEM ? 1 : 0;
 }
 

@@ -27,11 +27,35 @@ template <int N, int S> struct MhmLayout {
 
 // Physical flux along d of a global-frame face state (W primitive, U its
 // conserved form; energy U[4]).
-template <class T> __device__ __forceinline__ void pflux_global(const T W[5], const T U[5], int d, T F[5]) {
+template <int D, class T> __device__ __forceinline__ void pflux_global(const T W[5], const T U[5], T F[5]) {
   T wl[5], fl[5];
-  rot_in(W, wl, d);
+  rot_in<D>(W, wl);
   pflux(wl, U[4], fl);
-  rot_out(fl, F, d);
+  rot_out<D>(fl, F);
+}
+
+// Reconstruction along D of the cell (jj, ii) of plane p, its two face states
+// (conserved) and their physical fluxes along D.
+template <int D, int REC, class T, class WRing>
+__device__ __forceinline__ void mhm_faces(const WRing& Wr, int p, int jj, int ii, const Opts<T>& o, T Uf[2][5],
+                                          T Ff[2][5]) {
+  constexpr int S_ = REC == PPM ? 2 : 1;
+  T w[5][5], Wf[2][5], dW[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+#pragma unroll
+    for (int o2 = -S_; o2 <= S_; ++o2) {
+      if (D == 0) w[v][o2 + 2] = Wr(p, v, jj + S_, ii + S_ + o2);
+      else if (D == 1) w[v][o2 + 2] = Wr(p, v, jj + S_ + o2, ii + S_);
+      else w[v][o2 + 2] = Wr(p + o2, v, jj + S_, ii + S_);
+    }
+  }
+  recon5<REC>(w, o, Wf[0], Wf[1], dW);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    cons(Wf[s], Uf[s], o.gas);
+    pflux_global<D>(Wf[s], Uf[s], Ff[s]);
+  }
 }
 
 template <class T, class S, bool MIXED, int RS, int REC, int N>
@@ -58,25 +82,9 @@ __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
       for (int idx = threadIdx.x; idx < LL; idx += blockDim.x) {
         int jj = idx / L, ii = idx - jj * L;
         T Uf[3][2][5], Ff[3][2][5];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          T w[5][5], Wf[2][5], dW[5];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-#pragma unroll
-            for (int o2 = -S_; o2 <= S_; ++o2) {
-              if (d == 0) w[v][o2 + 2] = Wr(pB, v, jj + S_, ii + S_ + o2);
-              else if (d == 1) w[v][o2 + 2] = Wr(pB, v, jj + S_ + o2, ii + S_);
-              else w[v][o2 + 2] = Wr(pB + o2, v, jj + S_, ii + S_);
-            }
-          }
-          recon5<REC>(w, o, Wf[0], Wf[1], dW);
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            cons(Wf[s], Uf[d][s], o.gas);
-            pflux_global(Wf[s], Uf[d][s], d, Ff[d][s]);
-          }
-        }
+        mhm_faces<0, REC>(Wr, pB, jj, ii, o, Uf[0], Ff[0]);
+        mhm_faces<1, REC>(Wr, pB, jj, ii, o, Uf[1], Ff[1]);
+        mhm_faces<2, REC>(Wr, pB, jj, ii, o, Uf[2], Ff[2]);
         // S = dt/(2dx) (Fx(R) - Fx(L)) + dt/(2dy) (...) + dt/(2dz) (...)
 #pragma unroll
         for (int v = 0; v < 5; ++v) {

@@ -56,22 +56,26 @@ __device__ __forceinline__ float powv(float a, float b) { return powf(a, b); }
 __device__ __forceinline__ bool isnanv(double a) { return isnan(a); }
 __device__ __forceinline__ bool isnanv(float a) { return isnan(a); }
 
-__device__ __forceinline__ int tn(int d) { return 1 + d; }
-__device__ __forceinline__ int tt1(int d) { return 1 + (d == 2 ? 0 : d + 1); }
-__device__ __forceinline__ int tt2(int d) { return 1 + (d == 0 ? 2 : d - 1); }
+// Directions are compile-time constants everywhere so that the 5-vectors stay
+// in registers.
+template <int D> struct Dir {
+  static constexpr int n = 1 + D;
+  static constexpr int t1 = 1 + (D == 2 ? 0 : D + 1);
+  static constexpr int t2 = 1 + (D == 0 ? 2 : D - 1);
+};
 
-template <class T> __device__ __forceinline__ void rot_in(const T a[5], T b[5], int d) {
+template <int D, class T> __device__ __forceinline__ void rot_in(const T a[5], T b[5]) {
   b[0] = a[0];
-  b[1] = a[tn(d)];
-  b[2] = a[tt1(d)];
-  b[3] = a[tt2(d)];
+  b[1] = a[Dir<D>::n];
+  b[2] = a[Dir<D>::t1];
+  b[3] = a[Dir<D>::t2];
   b[4] = a[4];
 }
-template <class T> __device__ __forceinline__ void rot_out(const T b[5], T a[5], int d) {
+template <int D, class T> __device__ __forceinline__ void rot_out(const T b[5], T a[5]) {
   a[0] = b[0];
-  a[tn(d)] = b[1];
-  a[tt1(d)] = b[2];
-  a[tt2(d)] = b[3];
+  a[Dir<D>::n] = b[1];
+  a[Dir<D>::t1] = b[2];
+  a[Dir<D>::t2] = b[3];
   a[4] = b[4];
 }
 
@@ -130,28 +134,37 @@ template <class T> __device__ __forceinline__ T csound(T rho, T p, const Gas<T>&
 //   van Leer:   (2 dL dR) / (dL + dR)
 //   van Albada: (dL dR (dL + dR)) / (dL dL + dR dR)
 //   hybrid:     sign(dC) min(|theta dL|, |theta dR|, |dC|, |van Leer|)
-template <class T> __device__ __forceinline__ T slope(int lim, T theta, T dL, T dR) {
+// LIM >= 0 fixes the limiter at compile time; LIM = -1 reads `lim` at run time.
+// Evaluated without branches on the data (selects), so neighbouring cells of
+// a warp never diverge; the selected values are those of the formulas above.
+template <int LIM = -1, class T> __device__ __forceinline__ T slope(int lim, T theta, T dL, T dR) {
+  if (LIM >= 0) lim = LIM;
   T prod = dL * dR;
-  if (!(prod > T(0))) return T(0);
   T dC = T(0.5) * (dL + dR);
-  if (lim == LIM_VANLEER) return T(2) * prod / (dL + dR);
-  if (lim == LIM_VANALBADA) return prod * (dL + dR) / (dL * dL + dR * dR);
-  T m = absv(theta * dL);
-  T b = absv(theta * dR);
-  T c = absv(dC);
-  if (b < m) m = b;
-  if (c < m) m = c;
-  if (lim == LIM_HYBRID) {
-    T e = absv(T(2) * prod / (dL + dR));
-    if (e < m) m = e;
+  T r;
+  if (lim == LIM_VANLEER) {
+    r = T(2) * prod / (dL + dR);
+  } else if (lim == LIM_VANALBADA) {
+    r = prod * (dL + dR) / (dL * dL + dR * dR);
+  } else {
+    T m = absv(theta * dL);
+    T b = absv(theta * dR);
+    T c = absv(dC);
+    m = b < m ? b : m;
+    m = c < m ? c : m;
+    if (lim == LIM_HYBRID) {
+      T e = absv(T(2) * prod / (dL + dR));
+      m = e < m ? e : m;
+    }
+    r = dC > T(0) ? m : -m;
   }
-  return dC > T(0) ? m : -m;
+  return prod > T(0) ? r : T(0);
 }
 
 // PLM: wL = w0 - 0.5 d, wR = w0 + 0.5 d.
-template <class T>
+template <int LIM = -1, class T>
 __device__ __forceinline__ void plm(T wm, T w0, T wp, int lim, T theta, T& wL, T& wR, T& d) {
-  d = slope(lim, theta, w0 - wm, wp - w0);
+  d = slope<LIM>(lim, theta, w0 - wm, wp - w0);
   wL = w0 - T(0.5) * d;
   wR = w0 + T(0.5) * d;
 }
@@ -159,27 +172,23 @@ __device__ __forceinline__ void plm(T wm, T w0, T wp, int lim, T theta, T& wL, T
 // PPM (Colella & Woodward 1984): edges from limited slopes, then the
 // monotonicity constraints.
 //   L = 0.5 (w_{-1} + w_0) - (d_0 - d_{-1}) / 6,  R = 0.5 (w_0 + w_1) - (d_1 - d_0) / 6
-template <class T>
+template <int LIM = -1, class T>
 __device__ __forceinline__ void ppm(T wmm, T wm, T w0, T wp, T wpp, int lim, T theta, T& wL, T& wR) {
-  T dm = slope(lim, theta, wm - wmm, w0 - wm);
-  T d0 = slope(lim, theta, w0 - wm, wp - w0);
-  T dp = slope(lim, theta, wp - w0, wpp - wp);
+  T dm = slope<LIM>(lim, theta, wm - wmm, w0 - wm);
+  T d0 = slope<LIM>(lim, theta, w0 - wm, wp - w0);
+  T dp = slope<LIM>(lim, theta, wp - w0, wpp - wp);
   T L = T(0.5) * (wm + w0) - (d0 - dm) / T(6);
   T R = T(0.5) * (w0 + wp) - (dp - d0) / T(6);
-  if ((R - w0) * (w0 - L) <= T(0)) {
-    L = w0;
-    R = w0;
-  } else {
-    T dA = R - L;
-    T a6 = T(6) * (w0 - T(0.5) * (L + R));
-    if (dA * a6 > dA * dA) {
-      L = T(3) * w0 - T(2) * R;
-    } else if (-(dA * dA) > dA * a6) {
-      R = T(3) * w0 - T(2) * L;
-    }
-  }
-  wL = L;
-  wR = R;
+  // constraints as selects: local extremum -> flat; overshoot -> move one edge
+  const bool ext = (R - w0) * (w0 - L) <= T(0);
+  T dA = R - L;
+  T a6 = T(6) * (w0 - T(0.5) * (L + R));
+  const bool c1 = dA * a6 > dA * dA;
+  const bool c2 = !c1 && (-(dA * dA) > dA * a6);
+  T Ln = c1 ? T(3) * w0 - T(2) * R : L;
+  T Rn = c2 ? T(3) * w0 - T(2) * L : R;
+  wL = ext ? w0 : Ln;
+  wR = ext ? w0 : Rn;
 }
 
 // ------------------------------------------------- CTU characteristic tracing
@@ -242,7 +251,9 @@ template <class T> __device__ __forceinline__ void radd(const Eig<T>& e, int a, 
 // PLM tracing, "reference state" form (Colella 1990; Stone et al. 2008):
 //   Wr = W0 + (0.5 (1 - lamM dtdx)) dW + sum_{lam_a>0} ((0.5 dtdx) (lamM - lam_a)) (l_a.dW) r_a
 //   Wl = W0 - (0.5 (1 + lamm dtdx)) dW + sum_{lam_a<0} ((0.5 dtdx) (lamm - lam_a)) (l_a.dW) r_a
-// lamM = max(lam_5, 0), lamm = min(lam_1, 0); local frame.
+// lamM = max(lam_5, 0), lamm = min(lam_1, 0); local frame.  Each wave is
+// evaluated once with the coefficients of the side it travels to; the other
+// side receives an exact zero (no data-dependent branches).
 template <class T>
 __device__ __forceinline__ void trace_plm(const T W0[5], const T dW[5], T dtdx, const Gas<T>& g, T Wl[5], T Wr[5]) {
   Eig<T> e;
@@ -259,8 +270,11 @@ __device__ __forceinline__ void trace_plm(const T W0[5], const T dW[5], T dtdx, 
   T hdt = T(0.5) * dtdx;
 #pragma unroll
   for (int a = 0; a < 5; ++a) {
-    if (e.lam[a] > T(0)) radd(e, a, hdt * (lamM - e.lam[a]) * lproj(e, a, dW), Wr);
-    if (e.lam[a] < T(0)) radd(e, a, hdt * (lamm - e.lam[a]) * lproj(e, a, dW), Wl);
+    const T la = e.lam[a];
+    const bool pos = la > T(0), neg = la < T(0);
+    T coef = hdt * ((pos ? lamM : lamm) - la) * lproj(e, a, dW);
+    radd(e, a, pos ? coef : T(0), Wr);
+    radd(e, a, neg ? coef : T(0), Wl);
   }
 }
 
@@ -298,23 +312,17 @@ __device__ __forceinline__ void trace_ppm(const T W0[5], const T WL[5], const T 
   T tdt = T(1.0 / 3.0) * dtdx * dtdx;
 #pragma unroll
   for (int a = 0; a < 5; ++a) {
-    T la = e.lam[a];
-    if (la > T(0)) {
-      T c1 = hdt * (lamM - la);
-      T c2 = tdt * (lamM * lamM - la * la);
-      T X[5];
+    const T la = e.lam[a];
+    const bool pos = la > T(0), neg = la < T(0);
+    const T lref = pos ? lamM : lamm;
+    T c1 = hdt * (lref - la);
+    T c2 = tdt * (lref * lref - la * la);
+    T X[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) X[v] = c1 * (dA[v] - W6[v]) + c2 * W6[v];
-      radd(e, a, lproj(e, a, X), Wr);
-    }
-    if (la < T(0)) {
-      T c1 = hdt * (lamm - la);
-      T c2 = tdt * (lamm * lamm - la * la);
-      T X[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) X[v] = c1 * (dA[v] + W6[v]) + c2 * W6[v];
-      radd(e, a, lproj(e, a, X), Wl);
-    }
+    for (int v = 0; v < 5; ++v) X[v] = c1 * (pos ? dA[v] - W6[v] : dA[v] + W6[v]) + c2 * W6[v];
+    T coef = lproj(e, a, X);
+    radd(e, a, pos ? coef : T(0), Wr);
+    radd(e, a, neg ? coef : T(0), Wl);
   }
 }
 
@@ -386,26 +394,33 @@ template <class T> __device__ __forceinline__ void hllc(const Side<T>& L, const 
   T mL = L.W[0] * (SL - L.W[1]);
   T mR = R.W[0] * (SR - R.W[1]);
   T Ss = (R.W[4] - L.W[4] + mL * L.W[1] - mR * R.W[1]) / (mL - mR);
-  if (SL >= T(0)) {
+  // region: SL >= 0 -> FL; S* >= 0 -> left star; SR > 0 -> right star; else FR
+  const bool useL = SL >= T(0);
+  const bool left = Ss >= T(0);
+  const bool useR = !useL && !left && !(SR > T(0));
+  T SK = left ? SL : SR;
+  T mK = left ? mL : mR;
+  T uK = left ? L.W[1] : R.W[1];
+  T vK = left ? L.W[2] : R.W[2];
+  T wK = left ? L.W[3] : R.W[3];
+  T rK = left ? L.W[0] : R.W[0];
+  T pK = left ? L.W[4] : R.W[4];
+  T f = mK / (SK - Ss);
+  T Us[5], UK[5], FK[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] = L.F[v];
-  } else if (SR <= T(0) && !(Ss >= T(0))) {
+  for (int v = 0; v < 5; ++v) {
+    UK[v] = left ? L.U[v] : R.U[v];
+    FK[v] = left ? L.F[v] : R.F[v];
+  }
+  Us[0] = f;
+  Us[1] = f * Ss;
+  Us[2] = f * vK;
+  Us[3] = f * wK;
+  Us[4] = f * (UK[4] / rK + (Ss - uK) * (Ss + pK / mK));
 #pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] = R.F[v];
-  } else {
-    const bool left = Ss >= T(0);
-    const Side<T>& K = left ? L : R;
-    T SK = left ? SL : SR;
-    T mK = left ? mL : mR;
-    T f = mK / (SK - Ss);
-    T Us[5];
-    Us[0] = f;
-    Us[1] = f * Ss;
-    Us[2] = f * K.W[2];
-    Us[3] = f * K.W[3];
-    Us[4] = f * (K.U[4] / K.W[0] + (Ss - K.W[1]) * (Ss + K.W[4] / mK));
-#pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] = K.F[v] + SK * (Us[v] - K.U[v]);
+  for (int v = 0; v < 5; ++v) {
+    T Fs = FK[v] + SK * (Us[v] - UK[v]);
+    F[v] = useL ? L.F[v] : (useR ? R.F[v] : Fs);
   }
 }
 
@@ -432,15 +447,44 @@ __device__ __forceinline__ void exact_fk(T p, T rk, T pk, T ck, const Gas<T>& g,
   }
 }
 
-// Returns false on vacuum (pstar unset) or no convergence (pstar set).
+// Result of the out-of-line exact solver: flux and status bits.
+template <class T> struct Flux5 {
+  T F[5];
+  unsigned st;
+};
+template <class T> struct V5 {
+  T v[5];
+};
+
+// Exact flux from local primitives (W), sound speeds and total energies of
+// both sides.  On vacuum generation (no star state) the status gets
+// ST_EXACT_FAIL and the flux is the HLLE flux; on no convergence the status
+// gets ST_EXACT_FAIL and the last iterate is sampled.  Kept out of line and
+// fed by value: it is the slow reference solver (Sec. 2) and the rare
+// fallback path.
 template <class T>
-__device__ __noinline__ bool exact_flux(const Side<T>& L, const Side<T>& R, const Gas<T>& g, T F[5], bool& vacuum) {
+__device__ __noinline__ Flux5<T> exact_flux(V5<T> WLv, V5<T> WRv, T cL, T cR, T EL, T ER, Gas<T> g) {
+  Flux5<T> out;
+  out.st = 0;
+  Side<T> L, R;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    L.W[v] = WLv.v[v];
+    R.W[v] = WRv.v[v];
+  }
+  L.c = cL;
+  R.c = cR;
+  L.U[0] = L.W[0]; L.U[1] = L.W[0] * L.W[1]; L.U[2] = L.W[0] * L.W[2]; L.U[3] = L.W[0] * L.W[3]; L.U[4] = EL;
+  R.U[0] = R.W[0]; R.U[1] = R.W[0] * R.W[1]; R.U[2] = R.W[0] * R.W[2]; R.U[3] = R.W[0] * R.W[3]; R.U[4] = ER;
   T gam = g.gamma;
   T du = R.W[1] - L.W[1];
-  vacuum = false;
   if (T(2) / (gam - T(1)) * (L.c + R.c) <= du) {
-    vacuum = true;
-    return false;
+    // vacuum: the HLLE flux of the (unchanged) conserved states
+    pflux(L.W, EL, L.F);
+    pflux(R.W, ER, R.F);
+    out.st = ST_EXACT_FAIL;
+    hlle(L, R, g, out.F);
+    return out;
   }
   T ppv = T(0.5) * (L.W[4] + R.W[4]) - T(0.125) * du * (L.W[0] + R.W[0]) * (L.c + R.c);
   T pmin = T(1.0e-8) * T(0.5) * (L.W[4] + R.W[4]);
@@ -459,6 +503,7 @@ __device__ __noinline__ bool exact_flux(const Side<T>& L, const Side<T>& R, cons
       break;
     }
   }
+  if (!conv) out.st = ST_EXACT_FAIL;
   T fL, dfL, fR, dfR;
   exact_fk(p, L.W[0], L.W[4], L.c, g, fL, dfL);
   exact_fk(p, R.W[0], R.W[4], R.c, g, fR, dfR);
@@ -478,8 +523,7 @@ __device__ __noinline__ bool exact_flux(const Side<T>& L, const Side<T>& R, cons
   if (ps > K.W[4]) {  // shock
     T pr = ps / K.W[4];
     T SK = uK - K.c * sqrtv((gam + T(1)) / (T(2) * gam) * pr + (gam - T(1)) / (T(2) * gam));
-    bool outside = left ? (T(0) <= SK) : (T(0) <= SK);
-    if (outside) {
+    if (T(0) <= SK) {
       W[0] = K.W[0];
       W[1] = K.W[1];
       W[4] = K.W[4];
@@ -510,8 +554,22 @@ __device__ __noinline__ bool exact_flux(const Side<T>& L, const Side<T>& R, cons
     }
   }
   T E = W[4] / (gam - T(1)) + T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
-  pflux(W, E, F);
-  return conv;
+  pflux(W, E, out.F);
+  return out;
+}
+
+template <class T> __device__ __forceinline__ unsigned exact_call(const Side<T>& L, const Side<T>& R, const Gas<T>& g,
+                                                                  T F[5]) {
+  V5<T> a, b;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    a.v[v] = L.W[v];
+    b.v[v] = R.W[v];
+  }
+  Flux5<T> r = exact_flux(a, b, L.c, R.c, L.U[4], R.U[4], g);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) F[v] = r.F[v];
+  return r.st;
 }
 
 // Roe (1981) with the 3D wave strengths (Toro 2009 sec. 11.3); see the
@@ -565,48 +623,36 @@ template <class T> __device__ __forceinline__ bool roe(const Side<T>& L, const S
   return true;
 }
 
-// Fallback path kept out of line: it runs only where Roe fails.
-template <class T>
-__device__ __noinline__ unsigned roe_fallback_flux(const Side<T>& L, const Side<T>& R, const Gas<T>& g, int fb, T F[5]) {
-  unsigned st = ST_ROE_FALLBACK;
-  if (fb == RS_HLLC) {
-    hllc(L, R, g, F);
-  } else if (fb == RS_EXACT) {
-    bool vac;
-    if (!exact_flux(L, R, g, F, vac)) {
-      st |= ST_EXACT_FAIL;
-      if (vac) hlle(L, R, g, F);
-    }
-  } else {
-    hlle(L, R, g, F);
-  }
-  return st;
-}
-
-// Riemann flux along d for global-frame conserved states; returns status bits.
-template <class T, bool MIXED, int RS>
-__device__ __forceinline__ unsigned riemann(int d, const T ULg[5], const T URg[5], const Opts<T>& o, T Fg[5]) {
+// Riemann flux along D for global-frame conserved states; returns status
+// bits.  Where Roe fails, the fallback of Sec. 2 (HLLE / HLLC inline, the
+// exact solver out of line) gives the flux.
+template <class T, bool MIXED, int RS, int D>
+__device__ __forceinline__ unsigned riemann(const T ULg[5], const T URg[5], const Opts<T>& o, T Fg[5]) {
   T ul[5], ur[5], F[5];
-  rot_in(ULg, ul, d);
-  rot_in(URg, ur, d);
+  rot_in<D>(ULg, ul);
+  rot_in<D>(URg, ur);
   Side<T> L, R;
   mkside<T, MIXED>(ul, o.gas, L);
   mkside<T, MIXED>(ur, o.gas, R);
   unsigned st = 0;
   if (RS == RS_ROE) {
-    if (!roe(L, R, o.gas, F)) st = roe_fallback_flux(L, R, o.gas, o.fallback, F);
+    if (!roe(L, R, o.gas, F)) {
+      st = ST_ROE_FALLBACK;
+      if (o.fallback == RS_HLLC)
+        hllc(L, R, o.gas, F);
+      else if (o.fallback == RS_EXACT)
+        st |= exact_call(L, R, o.gas, F);
+      else
+        hlle(L, R, o.gas, F);
+    }
   } else if (RS == RS_HLLC) {
     hllc(L, R, o.gas, F);
   } else if (RS == RS_HLLE) {
     hlle(L, R, o.gas, F);
   } else {
-    bool vac;
-    if (!exact_flux(L, R, o.gas, F, vac)) {
-      st = ST_EXACT_FAIL;
-      if (vac) hlle(L, R, o.gas, F);
-    }
+    st = exact_call(L, R, o.gas, F);
   }
-  rot_out(F, Fg, d);
+  rot_out<D>(F, Fg);
   return st;
 }
 

@@ -62,7 +62,7 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
         UL[v] = R.XY(p, 0, 1, v, j + 1, f);
         UR[v] = R.XY(p, 0, 0, v, j + 1, f + 1);
       }
-      st |= riemann<T, MIXED, RS>(0, UL, UR, o, F);
+      st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
 #pragma unroll
       for (int v = 0; v < 5; ++v) R.F2x(p, v, j, f) = F[v];
       if (f == 0 || f == N) {
@@ -77,7 +77,7 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
         UL[v] = R.XY(p, 1, 1, v, f, i + 1);
         UR[v] = R.XY(p, 1, 0, v, f + 1, i + 1);
       }
-      st |= riemann<T, MIXED, RS>(1, UL, UR, o, F);
+      st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
 #pragma unroll
       for (int v = 0; v < 5; ++v) R.F2y(p, v, f, i) = F[v];
       if (f == 0 || f == N) {
@@ -92,7 +92,7 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
         UL[v] = R.Zs(p - 1, 1, v, j + 1, i + 1);
         UR[v] = R.Zs(p, 0, v, j + 1, i + 1);
       }
-      st |= riemann<T, MIXED, RS>(2, UL, UR, o, F);
+      st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
 #pragma unroll
       for (int v = 0; v < 5; ++v) R.F2z(p, v, j, i) = F[v];
       if (p == 0 || p == N) {
@@ -156,14 +156,14 @@ __device__ __forceinline__ void stage_load(const GroupCtx<T, S, N>& C, const Opt
 
 // Face values of one cell along d from a primitive ring (Sec. 2 step (1)):
 // w[] = the 2S+1 stencil values per variable, centre at index 2.
-template <int REC, class T>
+template <int REC, int LIM = -1, class T>
 __device__ __forceinline__ void recon5(const T w[5][5], const Opts<T>& o, T WLf[5], T WRf[5], T dW[5]) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     if (REC == PPM)
-      ppm(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4], o.limiter, o.theta, WLf[v], WRf[v]);
+      ppm<LIM>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4], o.limiter, o.theta, WLf[v], WRf[v]);
     else
-      plm(w[v][1], w[v][2], w[v][3], o.limiter, o.theta, WLf[v], WRf[v], dW[v]);
+      plm<LIM>(w[v][1], w[v][2], w[v][3], o.limiter, o.theta, WLf[v], WRf[v], dW[v]);
   }
 }
 

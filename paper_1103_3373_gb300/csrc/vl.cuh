@@ -89,7 +89,7 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
             UL[v] = Ur(pA, v, jj + 1, f);
             UR[v] = Ur(pA, v, jj + 1, f + 1);
           }
-          st |= riemann<T, MIXED, RS>(0, UL, UR, o, F);
+          st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
 #pragma unroll
           for (int v = 0; v < 5; ++v) F1.x(pA, v, jj, f) = F[v];
         } else if (idx < 2 * nx) {
@@ -100,7 +100,7 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
             UL[v] = Ur(pA, v, f, ii + 1);
             UR[v] = Ur(pA, v, f + 1, ii + 1);
           }
-          st |= riemann<T, MIXED, RS>(1, UL, UR, o, F);
+          st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
 #pragma unroll
           for (int v = 0; v < 5; ++v) F1.y(pA, v, f, ii) = F[v];
         } else {
@@ -111,7 +111,7 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
             UL[v] = Ur(pA - 1, v, jj + 1, ii + 1);
             UR[v] = Ur(pA, v, jj + 1, ii + 1);
           }
-          st |= riemann<T, MIXED, RS>(2, UL, UR, o, F);
+          st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
 #pragma unroll
           for (int v = 0; v < 5; ++v) F1.z(pA, v, jj, ii) = F[v];
         }
