@@ -65,6 +65,7 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge
 #define HYDRO_EUNSUPPORTED (-3) /* valid but not built (e.g. N other than 8, 16)  */
 #define HYDRO_ECUDA (-4)        /* a CUDA call failed (see hydro_last_cuda_error) */
 #define HYDRO_EWORKSPACE (-5)   /* workspace missing or smaller than required     */
+#define HYDRO_ETOOBIG (-6)      /* input larger than a fixed-size entry point takes */
 
 /* ---- per-group status bits (written, not OR-ed, once per group and call) --- */
 #define HYDRO_ST_ROE_FALLBACK 1u /* informational: Roe failed at >= 1 face and the
@@ -205,6 +206,33 @@ int hydro_cfl_dt(const void* U, int G, long long group_stride, long long var_str
  */
 int hydro_conserved_totals(const void* U, int G, long long group_stride, long long var_stride, long long cells,
                            int precision, double* totals_dev, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * hydro_cfl_dt_noalloc — hydro_cfl_dt for callers that cannot allocate device
+ * memory.  The paper has no counterpart: it serves code that runs where no
+ * allocator is reachable, e.g. a plug-in enqueued inside another framework's
+ * CUDA graph capture (where cudaMalloc is not allowed) or a host runtime
+ * that hands out only the input and output buffers.  It allocates nothing
+ * and calls no allocating routine: its scratch (one FP64 partial maximum per
+ * CTA) is a static device array of HYDRO_NOALLOC_MAX_PARTIALS doubles
+ * (64 KiB) that every GPU which loads the library keeps until the process
+ * exits.  Each CTA reduces HYDRO_NOALLOC_CELLS_PER_CTA cells, so G * cells
+ * may be at most HYDRO_NOALLOC_MAX_PARTIALS * HYDRO_NOALLOC_CELLS_PER_CTA
+ * (512^3); larger inputs return HYDRO_ETOOBIG before anything is launched.
+ *   Arguments, result and numerics are those of hydro_cfl_dt (dt_dev and
+ *   smax_dev are device outputs the caller provides); no workspace argument.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current) and caches it: make that first call before any
+ *   stream capture.  Every call shares the one array and leaves its partials
+ *   in it; nothing in it needs to start at zero (each call writes every
+ *   partial it reads).  Calls that overlap on the GPU (different streams or
+ *   host threads at once) race on the array: serialise them.
+ */
+#define HYDRO_NOALLOC_MAX_PARTIALS 8192
+#define HYDRO_NOALLOC_CELLS_PER_CTA 16384
+int hydro_cfl_dt_noalloc(const void* U, int G, long long group_stride, long long var_stride, long long cells,
+                         int precision, double gamma, double dens_floor, double pres_floor, const double* dx,
+                         double cfl, double* dt_dev, double* smax_dev, void* stream);
 
 /* Text for a return code. */
 const char* hydro_strerror(int code);

@@ -384,6 +384,7 @@ const char* hydro_strerror(int code) {
     case HYDRO_EUNSUPPORTED: return "configuration not built or not supported on this device";
     case HYDRO_ECUDA: return "CUDA call failed";
     case HYDRO_EWORKSPACE: return "workspace missing or too small";
+    case HYDRO_ETOOBIG: return "input larger than this fixed-size entry point takes";
     default: return "unknown error";
   }
 }

@@ -1,0 +1,153 @@
+// hydro_cfl_dt_noalloc: the CFL time-step reduction for callers that cannot
+// allocate device memory (a kernel plug-in running inside someone else's
+// CUDA graph capture, or a host framework whose allocator is unavailable in
+// the calling context).  It has no counterpart in the paper.
+//
+// Scratch: one FP64 partial maximum per CTA, in a file-scope static device
+// array of NOALLOC_MAX_PARTIALS entries (64 KiB), which every GPU that loads
+// the library keeps until the process exits.  Each CTA reduces a fixed chunk
+// of NOALLOC_CELLS_PER_CTA cells, so one call handles at most
+// NOALLOC_MAX_PARTIALS * NOALLOC_CELLS_PER_CTA = 512^3 cells; larger inputs
+// are rejected before anything is launched.
+//
+// In host code the array's name is only a host-side stand-in for the device
+// symbol, so its device address is looked up once per device, with that
+// device current, by cudaGetSymbolAddress, and that address is what the
+// kernels receive.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/hydro.h"
+#include "phys.cuh"
+
+namespace {
+
+constexpr int NOALLOC_MAX_PARTIALS = HYDRO_NOALLOC_MAX_PARTIALS;
+constexpr long long NOALLOC_CELLS_PER_CTA = HYDRO_NOALLOC_CELLS_PER_CTA;
+constexpr int NOALLOC_THREADS = 256;
+constexpr int NOALLOC_MAX_DEV = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_PARTIALS];
+
+std::mutex g_mu;
+double* g_partials_ptr[NOALLOC_MAX_DEV] = {nullptr};
+
+// Pass 1 (variant of the CFL partial reduction): CTA b reduces the cells
+// [b * NOALLOC_CELLS_PER_CTA, (b + 1) * NOALLOC_CELLS_PER_CTA) of the flat
+// (group, cell) range and writes its maximum of max_d (|v_d| + c) / dx_d to
+// part[b] (NaN if any of its cells gives NaN).
+template <class S>
+__global__ void __launch_bounds__(NOALLOC_THREADS)
+    noalloc_cfl_partial(const S* __restrict__ U, int G, long long gstride, long long vstride, long long cells,
+                        double gamma, double dfloor, double pfloor, double dx0, double dx1, double dx2,
+                        double* __restrict__ part) {
+  __shared__ double sh[NOALLOC_THREADS / 32];
+  __shared__ int anybad;
+  const long long total = (long long)G * cells;
+  const long long begin = (long long)blockIdx.x * NOALLOC_CELLS_PER_CTA;
+  long long end = begin + NOALLOC_CELLS_PER_CTA;
+  if (end > total) end = total;
+  if (threadIdx.x == 0) anybad = 0;
+  hyd::Gas<double> gas{gamma, gamma - 1.0, dfloor, pfloor};
+  double m = 0.0;
+  bool bad = false;
+  for (long long e = begin + threadIdx.x; e < end; e += NOALLOC_THREADS) {
+    long long gi = e / cells, i = e - gi * cells;
+    const S* b = U + gi * gstride + i;
+    double u[5], w[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = (double)b[v * vstride];
+    hyd::prim<double, false>(u, w, gas);
+    double c = sqrt(gamma * w[4] / w[0]);
+    double s = fmax((fabs(w[1]) + c) / dx0, fmax((fabs(w[2]) + c) / dx1, (fabs(w[3]) + c) / dx2));
+    if (isnan(s)) bad = true;
+    m = fmax(m, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();
+  if (bad) anybad = 1;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = sh[0];
+    for (int k = 1; k < NOALLOC_THREADS / 32; ++k) r = fmax(r, sh[k]);
+    part[blockIdx.x] = anybad ? __longlong_as_double(0x7ff8000000000000LL) : r;
+  }
+}
+
+// Pass 2: one CTA reduces the n partials and writes dt = cfl / max.
+__global__ void __launch_bounds__(1024) noalloc_cfl_final(const double* __restrict__ part, int n, double cfl,
+                                                           double* dt, double* smax) {
+  __shared__ double sh[32];
+  __shared__ int anybad;
+  if (threadIdx.x == 0) anybad = 0;
+  __syncthreads();
+  double m = 0.0;
+  bool bad = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = part[i];
+    if (isnan(v)) bad = true;
+    m = fmax(m, v);
+  }
+  if (bad) anybad = 1;
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = sh[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, sh[k]);
+    double mm = anybad ? __longlong_as_double(0x7ff8000000000000LL) : r;
+    *dt = cfl / mm;
+    if (smax) *smax = mm;
+  }
+}
+
+// Device address of the static partials for the current device (looked up
+// once per device, with that device current).
+int partials_for_current_device(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEV) return HYDRO_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_partials_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p) return HYDRO_ECUDA;
+    g_partials_ptr[dev] = (double*)p;
+  }
+  *out = g_partials_ptr[dev];
+  return HYDRO_OK;
+}
+
+bool pos_finite(double a) { return a > 0.0 && a < 1e300; }
+
+}  // namespace
+
+extern "C" int hydro_cfl_dt_noalloc(const void* U, int G, long long group_stride, long long var_stride,
+                                    long long cells, int precision, double gamma, double dens_floor,
+                                    double pres_floor, const double* dx, double cfl, double* dt_dev,
+                                    double* smax_dev, void* stream) {
+  if (!U || G < 0 || cells <= 0 || !dx || !dt_dev || !(gamma > 1.0) || !(cfl > 0.0)) return HYDRO_EINVAL;
+  if (precision < 0 || precision > 2) return HYDRO_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!pos_finite(dx[d])) return HYDRO_EINVAL;
+  if (G == 0) return HYDRO_EINVAL;
+  const long long total = (long long)G * cells;
+  if (total / G != cells || total > (long long)NOALLOC_MAX_PARTIALS * NOALLOC_CELLS_PER_CTA) return HYDRO_ETOOBIG;
+  double* part = nullptr;
+  int rc = partials_for_current_device(&part);
+  if (rc != HYDRO_OK) return rc;
+  const int nblk = (int)((total + NOALLOC_CELLS_PER_CTA - 1) / NOALLOC_CELLS_PER_CTA);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == HYDRO_FP64)
+    noalloc_cfl_partial<double><<<nblk, NOALLOC_THREADS, 0, st>>>((const double*)U, G, group_stride, var_stride,
+                                                                  cells, gamma, dens_floor, pres_floor, dx[0],
+                                                                  dx[1], dx[2], part);
+  else
+    noalloc_cfl_partial<float><<<nblk, NOALLOC_THREADS, 0, st>>>((const float*)U, G, group_stride, var_stride,
+                                                                 cells, gamma, dens_floor, pres_floor, dx[0], dx[1],
+                                                                 dx[2], part);
+  noalloc_cfl_final<<<1, 1024, 0, st>>>(part, nblk, cfl, dt_dev, smax_dev);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}

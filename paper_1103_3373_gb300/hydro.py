@@ -19,7 +19,8 @@ LIM_MINMOD, LIM_VANLEER, LIM_VANALBADA, LIM_HYBRID = 0, 1, 2, 3
 RS_EXACT, RS_HLLE, RS_HLLC, RS_ROE = 0, 1, 2, 3
 FP64, FP32, FP32_MIXED = 0, 1, 2
 BC_PERIODIC, BC_OUTFLOW = 0, 1
-OK, EINVAL, EGHOST, EUNSUPPORTED, ECUDA, EWORKSPACE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, EGHOST, EUNSUPPORTED, ECUDA, EWORKSPACE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6
+NOALLOC_MAX_PARTIALS, NOALLOC_CELLS_PER_CTA = 8192, 16384
 ST_ROE_FALLBACK, ST_NEG_DENS, ST_NEG_PRES, ST_NAN, ST_EXACT_FAIL = 1, 2, 4, 8, 16
 ST_ERROR_MASK = ST_NEG_DENS | ST_NEG_PRES | ST_NAN | ST_EXACT_FAIL
 MAX_LEVELS = 32
@@ -116,6 +117,8 @@ def _lib():
         L.hydro_cfl_dt.argtypes = [vp, i, ll, ll, ll, i, d, d, d, ctypes.POINTER(ctypes.c_double), d, vp, vp, vp,
                                    ctypes.c_size_t, vp]
         L.hydro_conserved_totals.argtypes = [vp, i, ll, ll, ll, i, vp, vp, ctypes.c_size_t, vp]
+        L.hydro_cfl_dt_noalloc.argtypes = [vp, i, ll, ll, ll, i, d, d, d, ctypes.POINTER(ctypes.c_double), d, vp,
+                                           vp, vp]
         L.hydro_strerror.argtypes = [i]
         L.hydro_strerror.restype = ctypes.c_char_p
         L.hydro_last_cuda_error.argtypes = []
@@ -277,3 +280,17 @@ def hydro_conserved_totals(U, totals_out, workspace, precision=FP32, stream=None
                                        _ptr(totals_out, "totals_out", "float64"), workspace.data_ptr(),
                                        workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "hydro_conserved_totals")
+
+
+def hydro_cfl_dt_noalloc(U, dx, cfl, dt_out, gamma=1.4, dens_floor=0.0, pres_floor=0.0, precision=FP32,
+                         smax_out=None, stream=None):
+    """hydro_cfl_dt without a workspace: for callers that cannot allocate
+    device memory (its scratch is a fixed static device array; at most
+    NOALLOC_MAX_PARTIALS * NOALLOC_CELLS_PER_CTA cells per call)."""
+    dt = _storage_dtype(precision)
+    G, gs, vs, cells = _red_layout(U)
+    dxa = (ctypes.c_double * 3)(*[float(a) for a in dx])
+    rc = _lib().hydro_cfl_dt_noalloc(_ptr(U, "U", dt), G, gs, vs, cells, precision, gamma, dens_floor, pres_floor,
+                                     dxa, float(cfl), _ptr(dt_out, "dt_out", "float64"),
+                                     _ptr(smax_out, "smax_out", "float64"), _stream(stream))
+    _check(rc, "hydro_cfl_dt_noalloc")
