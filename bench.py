@@ -153,6 +153,76 @@ def time_box(box, steps, warmup, torch, sampler=None):
     return step_ms, float(np.mean(adv_ms)), t0.elapsed_time(t1), clocks
 
 
+def amr_leg(H, RT, W, torch, dev, steps=20):
+    """AMR-shaped batch: 4 levels of 4096/2500/1500/800 halo-prepared groups
+    (refined where |grad rho|/rho > 0.3 on a seeded 128^3 lognormal root), per-
+    level dx and device dt.  FP32 batched persistent launch replayed from a
+    CUDA graph and autotuned, against the same FP32 step as one launch per
+    level and the plain FP64 per-level launch."""
+    t = time.perf_counter()
+    levels = W.amr_levels()
+    gen_s = time.perf_counter() - t
+    out = {"groups_per_level": [int(l["U"].shape[0]) for l in levels], "generate_s": gen_s,
+           "flagged_fraction": [l["flagged_fraction"] for l in levels]}
+    p = make_params(H, H.FP32, (1.0, 1.0, 1.0))
+    lb = RT.LevelBatch(levels, p, cfl=CFL, device=dev)
+    tb = lb.tune()
+    lb.capture()
+    cells = lb.cells
+    for _ in range(3):
+        lb.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        lb.replay()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    out["fp32_batched_graph"] = {"value": cells / (ms / 1e3), "ms_per_step": ms,
+                                 "block_threads": tb["block_threads"]}
+    for _ in range(2):
+        lb.step_per_level()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(5):
+        lb.step_per_level()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 5
+    out["fp32_per_level"] = {"value": cells / (ms / 1e3), "ms_per_step": ms}
+    del lb
+    torch.cuda.empty_cache()
+    lb = RT.LevelBatch(levels, make_params(H, H.FP64, (1.0, 1.0, 1.0)), cfl=CFL, device=dev)
+    lb.step_per_level()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(2):
+        lb.step_per_level()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 2
+    out["fp64_per_level"] = {"value": cells / (ms / 1e3), "ms_per_step": ms}
+    out["unit"] = UNIT
+    out["cells_per_step"] = cells
+    del lb
+    return out
+
+
+def serving_leg(H, torch, dev, n_requests=300):
+    """Serving: the first n_requests of the seeded Poisson stream (200/s;
+    boxes 32/64/128/256^3 with weights .4/.3/.2/.1; Mach 0.5-3; 5-50 steps;
+    FP32 CTU+PPM+Roe), admitted by an HBM budget of half the free memory."""
+    from paper_1103_3373_gb300 import serving as SV
+    from paper_1103_3373_gb300 import workloads as W
+    reqs = SV.requests_from_arrivals(W.poisson_arrivals(rate=200.0, n=n_requests, seed=6))
+    eng = SV.ServingEngine(make_params(H, H.FP32, (1.0, 1.0, 1.0)), device=dev)
+    summ = eng.run(reqs, realtime=True)
+    summ["unit"] = UNIT
+    summ["requests_offered"] = n_requests
+    return summ
+
+
 def cpu_baseline(U, dx, budget_s=12.0):
     """The FP64 oracle as it stands, OpenMP over patch groups on all host cores,
     on a bounded sample of the workload's groups (one step each)."""
@@ -268,6 +338,8 @@ def main():
     cells = N_BOX ** 3
     stream = torch.cuda.Stream(device=dev)
     box = RT.UniformBox(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev, stream=stream)
+    tuned = box.tune()
+    box.compute_dt()
     sampler = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -331,18 +403,29 @@ def main():
         torch.cuda.empty_cache()
         for name, prec, k in (("fp64", H.FP64, 4), ("mixed", H.FP32_MIXED, 50)):
             bx = RT.UniformBox(U, make_params(H, prec, dx), cfl=CFL, device=dev, stream=stream)
+            tb = bx.tune() if prec != H.FP64 else None
+            bx.compute_dt()
             sm, am, tm, _ = time_box(bx, k, 3, torch)
             extra[name] = {"value": cells * k / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / k,
-                           "kernel_ms": am, "steps": k}
+                           "kernel_ms": am, "steps": k,
+                           "block_threads": tb["block_threads"] if tb else bx.p.block_threads}
             del bx
             torch.cuda.empty_cache()
-        p = make_params(H, H.FP32, dx)
-        p.scheme, p.recon, p.riemann = H.VL, H.PLM, H.RS_HLLC
-        bx = RT.UniformBox(U, p, cfl=CFL, device=dev, stream=stream)
-        sm, am, tm, _ = time_box(bx, 50, 3, torch)
-        extra["vl_plm_hllc_fp32"] = {"value": cells * 50 / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / 50,
-                                     "kernel_ms": am}
-        del bx
+        for tag, sch, rec, rs in (("vl_plm_hllc_fp32", H.VL, H.PLM, H.RS_HLLC),
+                                  ("mhm_ppm_roe_fp32", H.MHM, H.PPM, H.RS_ROE)):
+            p = make_params(H, H.FP32, dx)
+            p.scheme, p.recon, p.riemann = sch, rec, rs
+            bx = RT.UniformBox(U, p, cfl=CFL, device=dev, stream=stream)
+            tb = bx.tune()
+            bx.compute_dt()
+            sm, am, tm, _ = time_box(bx, 50, 3, torch)
+            extra[tag] = {"value": cells * 50 / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / 50,
+                          "kernel_ms": am, "block_threads": tb["block_threads"]}
+            del bx
+        torch.cuda.empty_cache()
+        extra["amr_levels"] = amr_leg(H, RT, W, torch, dev)
+        torch.cuda.empty_cache()
+        extra["serving"] = serving_leg(H, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -355,7 +438,8 @@ def main():
                 "config": dict(CONFIG, parallelism="replicas%d" % world if world > 1 else "single GPU"),
                 "p50_step_ms": RT.percentile(step_ms, 50), "p99_step_ms": RT.percentile(step_ms, 99),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 3 * args.steps, "status_error_groups": int(np.count_nonzero(st & H.ST_ERROR_MASK)),
+                "gpu_launches": 3 * args.steps, "autotuned": {"block_threads": tuned["block_threads"],
+                                                              "grid_ctas": tuned["grid_ctas"]}, "status_error_groups": int(np.count_nonzero(st & H.ST_ERROR_MASK)),
                 "state_finite": finite, "extra": extra,
                 "paper_context": "3.0e7 cell-updates/s, CTU+PPM+Roe FP32 on one Tesla C2050 incl. transfers "
                                  "(Sec. 3.2); other hardware, not a target"}

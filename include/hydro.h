@@ -185,8 +185,9 @@ int hydro_advance_levels(const hydro_params* p, const hydro_level* levels, int n
 /*
  * hydro_cfl_dt — evolution time step (Sec. 4.3) as a device reduction:
  *   dt = cfl / max over cells of max_d (|v_d| + c) / dx_d,  c = sqrt(gamma p / rho),
- * with primitives recovered with the floors.  The maximum is reduced in FP64
- * for every precision.
+ * with primitives recovered with the floors.  The per-cell speeds are
+ * evaluated in the storage precision; the maxima, the division by dx and dt
+ * in FP64 (for FP64 data the result is exactly the FP64 formula above).
  *   U        device, element (g, v, i) at U[g*group_stride + v*var_stride + i],
  *            i < cells, g < G (a field: G = 1, var_stride = cells = X*Y*Z).
  *   dt_dev   device double[1]: receives dt.  smax_dev (optional) receives the
@@ -213,12 +214,14 @@ int hydro_conserved_totals(const void* U, int G, long long group_stride, long lo
  * allocator is reachable, e.g. a plug-in enqueued inside another framework's
  * CUDA graph capture (where cudaMalloc is not allowed) or a host runtime
  * that hands out only the input and output buffers.  It allocates nothing
- * and calls no allocating routine: its scratch (one FP64 partial maximum per
- * CTA) is a static device array of HYDRO_NOALLOC_MAX_PARTIALS doubles
- * (64 KiB) that every GPU which loads the library keeps until the process
- * exits.  Each CTA reduces HYDRO_NOALLOC_CELLS_PER_CTA cells, so G * cells
- * may be at most HYDRO_NOALLOC_MAX_PARTIALS * HYDRO_NOALLOC_CELLS_PER_CTA
- * (512^3); larger inputs return HYDRO_ETOOBIG before anything is launched.
+ * and calls no allocating routine: its scratch (three FP64 partial maxima
+ * per CTA, one per direction) is a static device array of
+ * HYDRO_NOALLOC_MAX_PARTIALS doubles (64 KiB) that every GPU which loads the
+ * library keeps until the process exits.  Each CTA reduces
+ * HYDRO_NOALLOC_CELLS_PER_CTA cells, so G * cells may be at most
+ * (HYDRO_NOALLOC_MAX_PARTIALS / 3) * HYDRO_NOALLOC_CELLS_PER_CTA (1.79e8; a
+ * 512^3 box fits); larger inputs return HYDRO_ETOOBIG before anything is
+ * launched.
  *   Arguments, result and numerics are those of hydro_cfl_dt (dt_dev and
  *   smax_dev are device outputs the caller provides); no workspace argument.
  *   The first call on a device looks up the array's device address (with
@@ -229,7 +232,7 @@ int hydro_conserved_totals(const void* U, int G, long long group_stride, long lo
  *   host threads at once) race on the array: serialise them.
  */
 #define HYDRO_NOALLOC_MAX_PARTIALS 8192
-#define HYDRO_NOALLOC_CELLS_PER_CTA 16384
+#define HYDRO_NOALLOC_CELLS_PER_CTA 65536
 int hydro_cfl_dt_noalloc(const void* U, int G, long long group_stride, long long var_stride, long long cells,
                          int precision, double gamma, double dens_floor, double pres_floor, const double* dx,
                          double cfl, double* dt_dev, double* smax_dev, void* stream);

@@ -2,7 +2,8 @@
 //   * ghost-zone gather of halo-padded groups from a uniform field (the
 //     "preparation step" of Sec. 4.2, on the device);
 //   * CFL time step (the evolution time step of Sec. 4.3) as a two-pass
-//     FP64 max-reduction;
+//     max-reduction (per-cell speeds in the storage precision, maxima and the
+//     final dt in FP64);
 //   * FP64 totals of the conserved variables (conservation monitor).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -73,62 +74,78 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// Pass 1: per-CTA maximum of max_d (|v_d| + c) / dx_d, evaluated in FP64.
-// A NaN cell makes the maximum NaN (so dt becomes NaN and is noticed).
+// Pass 1: per CTA and direction d, the maximum over cells of |v_d| + c
+// (c = sqrt(gamma p / rho), primitives with floors), evaluated in the storage
+// precision and kept as FP64; part[d * gridDim.x + b].  Division by dx_d
+// comes once, in pass 2: max_cells((|v_d| + c) / dx_d) equals
+// (max_cells(|v_d| + c)) / dx_d because rounded division by a positive number
+// is monotone.  A NaN cell makes the CTA's partials NaN.
 template <class S>
 __global__ void cfl_partial_kernel(const S* __restrict__ U, int G, long long gstride, long long vstride,
-                                   long long cells, double gamma, double dfloor, double pfloor, double dx0,
-                                   double dx1, double dx2, double* __restrict__ part) {
+                                   long long cells, double gamma, double dfloor, double pfloor,
+                                   double* __restrict__ part) {
   __shared__ double sh[32];
+  __shared__ int anybad;
+  if (threadIdx.x == 0) anybad = 0;
   const long long total = (long long)G * cells;
-  double m = 0.0;
+  S m[3] = {S(0), S(0), S(0)};
   bool bad = false;
-  Gas<double> gas{gamma, gamma - 1.0, dfloor, pfloor};
+  Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor};
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     long long gi = e / cells, i = e - gi * cells;
     const S* b = U + gi * gstride + i;
-    double u[5], w[5];
+    S u[5], w[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) u[v] = (double)b[v * vstride];
-    prim<double, false>(u, w, gas);
-    double c = sqrt(gamma * w[4] / w[0]);
-    double s0 = (fabs(w[1]) + c) / dx0;
-    double s1 = (fabs(w[2]) + c) / dx1;
-    double s2 = (fabs(w[3]) + c) / dx2;
-    double s = fmax(s0, fmax(s1, s2));
-    if (isnan(s)) bad = true;
-    m = fmax(m, s);
+    for (int v = 0; v < 5; ++v) u[v] = b[v * vstride];
+    prim<S, false>(u, w, gas);
+    S c = sqrtv(gas.gamma * w[4] / w[0]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      S s = absv(w[1 + d]) + c;
+      if (isnanv(s)) bad = true;
+      m[d] = s > m[d] ? s : m[d];
+    }
   }
-  m = block_max(m, sh);
-  __syncthreads();
-  __shared__ int anybad;
-  if (threadIdx.x == 0) anybad = 0;
   __syncthreads();
   if (bad) anybad = 1;
-  __syncthreads();
-  if (threadIdx.x == 0) part[blockIdx.x] = anybad ? __longlong_as_double(0x7ff8000000000000LL) : m;
+  for (int d = 0; d < 3; ++d) {
+    double r = block_max((double)m[d], sh);
+    __syncthreads();
+    if (threadIdx.x == 0) part[d * gridDim.x + blockIdx.x] = anybad ? __longlong_as_double(0x7ff8000000000000LL) : r;
+  }
 }
 
-// Pass 2: one CTA reduces the partials and writes dt = cfl / max.
-__global__ void cfl_final_kernel(const double* __restrict__ part, int n, double cfl, double* dt, double* smax) {
+// Pass 2: one CTA reduces the partials and writes
+//   smax = max_d (max speed_d) / dx_d,   dt = cfl / smax.
+__global__ void cfl_final_kernel(const double* __restrict__ part, int n, double dx0, double dx1, double dx2,
+                                 double cfl, double* dt, double* smax) {
   __shared__ double sh[32];
-  double m = 0.0;
-  bool bad = false;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = part[i];
-    if (isnan(v)) bad = true;
-    m = fmax(m, v);
-  }
-  m = block_max(m, sh);
   __shared__ int anybad;
-  __syncthreads();
+  __shared__ double md[3];
   if (threadIdx.x == 0) anybad = 0;
   __syncthreads();
-  if (bad) anybad = 1;
-  __syncthreads();
+  for (int d = 0; d < 3; ++d) {
+    double m = 0.0;
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double v = part[d * n + i];
+      if (isnan(v)) bad = true;
+      m = fmax(m, v);
+    }
+    if (bad) anybad = 1;
+    m = block_max(m, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) md[d] = m;
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double mm = anybad ? __longlong_as_double(0x7ff8000000000000LL) : m;
+    double s = md[0] / dx0;
+    double s1 = md[1] / dx1;
+    double s2 = md[2] / dx2;
+    s = s1 > s ? s1 : s;
+    s = s2 > s ? s2 : s;
+    double mm = anybad ? __longlong_as_double(0x7ff8000000000000LL) : s;
     *dt = cfl / mm;
     if (smax) *smax = mm;
   }
@@ -195,12 +212,10 @@ cudaError_t launch_cfl(const void* U, int G, long long gs, long long vs, long lo
   if (grid < 1) grid = 1;
   if (grid > RED_MAX_CTAS) grid = RED_MAX_CTAS;
   if (dbl)
-    cfl_partial_kernel<double><<<grid, threads, 0, st>>>((const double*)U, G, gs, vs, cells, gamma, dfl, pfl,
-                                                         dx[0], dx[1], dx[2], ws);
+    cfl_partial_kernel<double><<<grid, threads, 0, st>>>((const double*)U, G, gs, vs, cells, gamma, dfl, pfl, ws);
   else
-    cfl_partial_kernel<float><<<grid, threads, 0, st>>>((const float*)U, G, gs, vs, cells, gamma, dfl, pfl,
-                                                        dx[0], dx[1], dx[2], ws);
-  cfl_final_kernel<<<1, 1024, 0, st>>>(ws, grid, cfl, dt, smax);
+    cfl_partial_kernel<float><<<grid, threads, 0, st>>>((const float*)U, G, gs, vs, cells, gamma, dfl, pfl, ws);
+  cfl_final_kernel<<<1, 1024, 0, st>>>(ws, grid, dx[0], dx[1], dx[2], cfl, dt, smax);
   return cudaGetLastError();
 }
 

@@ -99,6 +99,39 @@ __device__ __forceinline__ void trace_cell(const WRing& Wr, int p, int jj, int i
   cons(wg, Ur, o.gas);
 }
 
+// The same for a direction known only at run time (one inlined copy).
+template <int REC, int LIM, class T, class WRing>
+__device__ __forceinline__ void trace_cell_rt(const WRing& Wr, int p, int jj, int ii, int d, const Opts<T>& o, T dtdx,
+                                              T Ul[5], T Ur[5]) {
+  constexpr int S_ = REC == PPM ? 2 : 1;
+  const int sx = d == 0, sy = d == 1, sz = d == 2;
+  T w[5][5], WLf[5], WRf[5], dW[5], W0[5];
+#pragma unroll
+  for (int o2 = -S_; o2 <= S_; ++o2) {
+    const T* base = &Wr(p + sz * o2, 0, jj + S_ + sy * o2, ii + S_ + sx * o2);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) w[v][o2 + 2] = base[v * WRing::PL / 5];
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) W0[v] = w[v][2];
+  recon5<REC, LIM>(w, o, WLf, WRf, dW);
+  T w0l[5], a[5], b[5], tl[5], tr[5];
+  rot_in_rt(W0, w0l, d);
+  if (REC == PPM) {
+    rot_in_rt(WLf, a, d);
+    rot_in_rt(WRf, b, d);
+    trace_ppm(w0l, a, b, dtdx, o.gas, tl, tr);
+  } else {
+    rot_in_rt(dW, a, d);
+    trace_plm(w0l, a, dtdx, o.gas, tl, tr);
+  }
+  T wg[5];
+  rot_out_rt(tl, wg, d);
+  cons(wg, Ul, o.gas);
+  rot_out_rt(tr, wg, d);
+  cons(wg, Ur, o.gas);
+}
+
 // Transverse flux-gradient correction (step (3)) of one face state:
 //   u = (u - h1 (G1+ - G1-)) - h2 (G2+ - G2-), the two other directions in
 //   increasing order.
@@ -148,27 +181,14 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           int rem = k - d * LL;
           int jj = rem / L, ii = rem - jj * L;
           T Ul[5], Ur[5];
-          if (d == 0) {
-            trace_cell<0, REC, LIM>(Wr, q, jj, ii, o, C.dtdx[0], Ul, Ur);
+          trace_cell_rt<REC, LIM>(Wr, q, jj, ii, d, o, d == 0 ? C.dtdx[0] : (d == 1 ? C.dtdx[1] : C.dtdx[2]), Ul,
+                                  Ur);
+          T* dl = d < 2 ? &R.XY(q, d, 0, 0, jj, ii) : &R.Zs(q, 0, 0, jj, ii);
+          T* dr = d < 2 ? &R.XY(q, d, 1, 0, jj, ii) : &R.Zs(q, 1, 0, jj, ii);
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              R.XY(q, 0, 0, v, jj, ii) = Ul[v];
-              R.XY(q, 0, 1, v, jj, ii) = Ur[v];
-            }
-          } else if (d == 1) {
-            trace_cell<1, REC, LIM>(Wr, q, jj, ii, o, C.dtdx[1], Ul, Ur);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              R.XY(q, 1, 0, v, jj, ii) = Ul[v];
-              R.XY(q, 1, 1, v, jj, ii) = Ur[v];
-            }
-          } else {
-            trace_cell<2, REC, LIM>(Wr, q, jj, ii, o, C.dtdx[2], Ul, Ur);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              R.Zs(q, 0, v, jj, ii) = Ul[v];
-              R.Zs(q, 1, v, jj, ii) = Ur[v];
-            }
+          for (int v = 0; v < 5; ++v) {
+            dl[v * LL] = Ul[v];
+            dr[v * LL] = Ur[v];
           }
         }
       }
@@ -193,40 +213,43 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
       const int nz = q >= 0 ? LL : 0;
       const int cnt = 2 * NX + nz;
       for (int idx = tid; idx < cnt; idx += nthr) {
-        T UL[5], UR[5], F[5];
+        // the two states (stride LL between variables) and the flux slot
+        const T *pl, *pr;
+        T* pf;
+        int fs, d;
         if (idx < NX) {
           int jj = idx / (N + 1), f = idx - jj * (N + 1);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = R.XY(q, 0, 1, v, jj, f);
-            UR[v] = R.XY(q, 0, 0, v, jj, f + 1);
-          }
-          st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F1.x(q, v, jj, f) = F[v];
+          d = 0;
+          pl = &R.XY(q, 0, 1, 0, jj, f);
+          pr = &R.XY(q, 0, 0, 0, jj, f + 1);
+          pf = &F1.x(q, 0, jj, f);
+          fs = L * (N + 1);
         } else if (idx < 2 * NX) {
           int k = idx - NX;
           int f = k / L, ii = k - f * L;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = R.XY(q, 1, 1, v, f, ii);
-            UR[v] = R.XY(q, 1, 0, v, f + 1, ii);
-          }
-          st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F1.y(q, v, f, ii) = F[v];
+          d = 1;
+          pl = &R.XY(q, 1, 1, 0, f, ii);
+          pr = &R.XY(q, 1, 0, 0, f + 1, ii);
+          pf = &F1.y(q, 0, f, ii);
+          fs = (N + 1) * L;
         } else {
           int k = idx - 2 * NX;
           int jj = k / L, ii = k - jj * L;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = R.Zs(q - 1, 1, v, jj, ii);
-            UR[v] = R.Zs(q, 0, v, jj, ii);
-          }
-          st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F1.z(q, v, jj, ii) = F[v];
+          d = 2;
+          pl = &R.Zs(q - 1, 1, 0, jj, ii);
+          pr = &R.Zs(q, 0, 0, jj, ii);
+          pf = &F1.z(q, 0, jj, ii);
+          fs = LL;
         }
+        T UL[5], UR[5], F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          UL[v] = pl[v * LL];
+          UR[v] = pr[v * LL];
+        }
+        st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
       }
     }
     __syncthreads();
@@ -246,60 +269,100 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
         C.load5(ii - 1 - S_, jj - 1 - S_, pa, Ua0);
       }
       for (int idx = tid; idx < ne; idx += nthr) {
-        T UL[5], UR[5], F[5];
+        // per item: the two face states, the four stage-1 flux pairs that
+        // correct them (first transverse direction e1, second e2), the flux
+        // slot and the boundary face it may belong to
+        const T *sl, *sr, *a1p, *a1m, *a2p, *a2m, *b1p, *b1m, *b2p, *b2m;
+        T* pf;
+        T g1, g2;
+        int d, fs, bface = -1, ba = 0, bb = 0;
         if (idx < nx) {
           // x face f of row j: R state of cell f-1 and L state of cell f
           int j = idx / (N + 1), f = idx - j * (N + 1), jj = j + 1;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = correct(R.XY(r, 0, 1, v, jj, f), h1, F1.y(r, v, jj, f), F1.y(r, v, jj - 1, f), h2,
-                            F1.z(r + 1, v, jj, f), F1.z(r, v, jj, f));
-            UR[v] = correct(R.XY(r, 0, 0, v, jj, f + 1), h1, F1.y(r, v, jj, f + 1), F1.y(r, v, jj - 1, f + 1), h2,
-                            F1.z(r + 1, v, jj, f + 1), F1.z(r, v, jj, f + 1));
-          }
-          st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) R.F2x(r, v, j, f) = F[v];
+          d = 0;
+          g1 = h1;
+          g2 = h2;
+          sl = &R.XY(r, 0, 1, 0, jj, f);
+          sr = &R.XY(r, 0, 0, 0, jj, f + 1);
+          a1p = &F1.y(r, 0, jj, f);
+          a1m = &F1.y(r, 0, jj - 1, f);
+          a2p = &F1.z(r + 1, 0, jj, f);
+          a2m = &F1.z(r, 0, jj, f);
+          b1p = &F1.y(r, 0, jj, f + 1);
+          b1m = &F1.y(r, 0, jj - 1, f + 1);
+          b2p = &F1.z(r + 1, 0, jj, f + 1);
+          b2m = &F1.z(r, 0, jj, f + 1);
+          pf = &R.F2x(r, 0, j, f);
+          fs = N * (N + 1);
           if (f == 0 || f == N) {
-#pragma unroll
-            for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 0 : 1, v, r, j, F[v]);
+            bface = f == 0 ? 0 : 1;
+            ba = r;
+            bb = j;
           }
         } else if (idx < 2 * nx) {
           // y face f of column i: R state of cell f-1 and L state of cell f
           int k = idx - nx;
           int f = k / N, i = k - f * N, ii = i + 1;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = correct(R.XY(r, 1, 1, v, f, ii), h0, F1.x(r, v, f, ii), F1.x(r, v, f, ii - 1), h2,
-                            F1.z(r + 1, v, f, ii), F1.z(r, v, f, ii));
-            UR[v] = correct(R.XY(r, 1, 0, v, f + 1, ii), h0, F1.x(r, v, f + 1, ii), F1.x(r, v, f + 1, ii - 1), h2,
-                            F1.z(r + 1, v, f + 1, ii), F1.z(r, v, f + 1, ii));
-          }
-          st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) R.F2y(r, v, f, i) = F[v];
+          d = 1;
+          g1 = h0;
+          g2 = h2;
+          sl = &R.XY(r, 1, 1, 0, f, ii);
+          sr = &R.XY(r, 1, 0, 0, f + 1, ii);
+          a1p = &F1.x(r, 0, f, ii);
+          a1m = &F1.x(r, 0, f, ii - 1);
+          a2p = &F1.z(r + 1, 0, f, ii);
+          a2m = &F1.z(r, 0, f, ii);
+          b1p = &F1.x(r, 0, f + 1, ii);
+          b1m = &F1.x(r, 0, f + 1, ii - 1);
+          b2p = &F1.z(r + 1, 0, f + 1, ii);
+          b2m = &F1.z(r, 0, f + 1, ii);
+          pf = &R.F2y(r, 0, f, i);
+          fs = (N + 1) * N;
           if (f == 0 || f == N) {
-#pragma unroll
-            for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 2 : 3, v, r, i, F[v]);
+            bface = f == 0 ? 2 : 3;
+            ba = r;
+            bb = i;
           }
         } else {
           // z face below plane r: R state of plane r-1 and L state of plane r
           int k = idx - 2 * nx;
           int j = k / N, i = k - j * N, jj = j + 1, ii = i + 1;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = correct(R.Zs(r - 1, 1, v, jj, ii), h0, F1.x(r - 1, v, jj, ii), F1.x(r - 1, v, jj, ii - 1), h1,
-                            F1.y(r - 1, v, jj, ii), F1.y(r - 1, v, jj - 1, ii));
-            UR[v] = correct(R.Zs(r, 0, v, jj, ii), h0, F1.x(r, v, jj, ii), F1.x(r, v, jj, ii - 1), h1,
-                            F1.y(r, v, jj, ii), F1.y(r, v, jj - 1, ii));
-          }
-          st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) R.F2z(r, v, j, i) = F[v];
+          d = 2;
+          g1 = h0;
+          g2 = h1;
+          sl = &R.Zs(r - 1, 1, 0, jj, ii);
+          sr = &R.Zs(r, 0, 0, jj, ii);
+          a1p = &F1.x(r - 1, 0, jj, ii);
+          a1m = &F1.x(r - 1, 0, jj, ii - 1);
+          a2p = &F1.y(r - 1, 0, jj, ii);
+          a2m = &F1.y(r - 1, 0, jj - 1, ii);
+          b1p = &F1.x(r, 0, jj, ii);
+          b1m = &F1.x(r, 0, jj, ii - 1);
+          b2p = &F1.y(r, 0, jj, ii);
+          b2m = &F1.y(r, 0, jj - 1, ii);
+          pf = &R.F2z(r, 0, j, i);
+          fs = N * N;
           if (r == 0 || r == N) {
-#pragma unroll
-            for (int v = 0; v < 5; ++v) C.store_flux(r == 0 ? 4 : 5, v, j, i, F[v]);
+            bface = r == 0 ? 4 : 5;
+            ba = j;
+            bb = i;
           }
+        }
+        // variable strides of the stage-1 flux arrays used for e1 and e2
+        const int s1 = d == 0 ? (N + 1) * L : L * (N + 1);
+        const int s2 = d == 2 ? (N + 1) * L : LL;
+        T UL[5], UR[5], F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          UL[v] = correct(sl[v * LL], g1, a1p[v * s1], a1m[v * s1], g2, a2p[v * s2], a2m[v * s2]);
+          UR[v] = correct(sr[v * LL], g1, b1p[v * s1], b1m[v * s1], g2, b2p[v * s2], b2m[v * s2]);
+        }
+        st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
+        if (bface >= 0) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) C.store_flux(bface, v, ba, bb, F[v]);
         }
       }
       for (int k = tid; k < na; k += nthr) {

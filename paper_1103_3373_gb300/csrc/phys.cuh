@@ -79,6 +79,24 @@ template <int D, class T> __device__ __forceinline__ void rot_out(const T b[5], 
   a[4] = b[4];
 }
 
+// Run-time direction: the same permutations written as selects, so one
+// inlined copy of a solver serves all three directions (the kernels stay
+// small enough for the instruction caches).
+template <class T> __device__ __forceinline__ void rot_in_rt(const T a[5], T b[5], int d) {
+  b[0] = a[0];
+  b[1] = d == 0 ? a[1] : (d == 1 ? a[2] : a[3]);
+  b[2] = d == 0 ? a[2] : (d == 1 ? a[3] : a[1]);
+  b[3] = d == 0 ? a[3] : (d == 1 ? a[1] : a[2]);
+  b[4] = a[4];
+}
+template <class T> __device__ __forceinline__ void rot_out_rt(const T b[5], T a[5], int d) {
+  a[0] = b[0];
+  a[1] = d == 0 ? b[1] : (d == 1 ? b[3] : b[2]);
+  a[2] = d == 0 ? b[2] : (d == 1 ? b[1] : b[3]);
+  a[3] = d == 0 ? b[3] : (d == 1 ? b[2] : b[1]);
+  a[4] = b[4];
+}
+
 // ------------------------------------------------------------- EOS
 // U -> W in the frame U is given in:
 //   rho = max(U0, floor); kin = (0.5 * ((U1*U1 + U2*U2) + U3*U3)) / rho;
@@ -653,6 +671,37 @@ __device__ __forceinline__ unsigned riemann(const T ULg[5], const T URg[5], cons
     st = exact_call(L, R, o.gas, F);
   }
   rot_out<D>(F, Fg);
+  return st;
+}
+
+// Same as riemann<..., D> for a direction known only at run time.
+template <class T, bool MIXED, int RS>
+__device__ __forceinline__ unsigned riemann_rt(int d, const T ULg[5], const T URg[5], const Opts<T>& o, T Fg[5]) {
+  T ul[5], ur[5], F[5];
+  rot_in_rt(ULg, ul, d);
+  rot_in_rt(URg, ur, d);
+  Side<T> L, R;
+  mkside<T, MIXED>(ul, o.gas, L);
+  mkside<T, MIXED>(ur, o.gas, R);
+  unsigned st = 0;
+  if (RS == RS_ROE) {
+    if (!roe(L, R, o.gas, F)) {
+      st = ST_ROE_FALLBACK;
+      if (o.fallback == RS_HLLC)
+        hllc(L, R, o.gas, F);
+      else if (o.fallback == RS_EXACT)
+        st |= exact_call(L, R, o.gas, F);
+      else
+        hlle(L, R, o.gas, F);
+    }
+  } else if (RS == RS_HLLC) {
+    hllc(L, R, o.gas, F);
+  } else if (RS == RS_HLLE) {
+    hlle(L, R, o.gas, F);
+  } else {
+    st = exact_call(L, R, o.gas, F);
+  }
+  rot_out_rt(F, Fg, d);
   return st;
 }
 

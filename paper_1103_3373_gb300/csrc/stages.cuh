@@ -50,55 +50,65 @@ template <class T, int N, int DXY, int DZ> struct FaceRings {
 // 0 <= p <= N).  Fluxes on the group boundary are stored at once (step (5)).
 template <class T, class S, bool MIXED, int RS, int N, class FR>
 __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p) {
+  constexpr int LL = FR::LL;
   unsigned st = 0;
   const int nx = (p < N) ? N * (N + 1) : 0;
   const int cnt = 2 * nx + N * N;
   for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-    T UL[5], UR[5], F[5];
+    const T *pl, *pr;
+    T* pf;
+    int d, fs, bface = -1, ba = 0, bb = 0;
     if (idx < nx) {
       int j = idx / (N + 1), f = idx - j * (N + 1);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        UL[v] = R.XY(p, 0, 1, v, j + 1, f);
-        UR[v] = R.XY(p, 0, 0, v, j + 1, f + 1);
-      }
-      st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) R.F2x(p, v, j, f) = F[v];
+      d = 0;
+      pl = &R.XY(p, 0, 1, 0, j + 1, f);
+      pr = &R.XY(p, 0, 0, 0, j + 1, f + 1);
+      pf = &R.F2x(p, 0, j, f);
+      fs = N * (N + 1);
       if (f == 0 || f == N) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 0 : 1, v, p, j, F[v]);
+        bface = f == 0 ? 0 : 1;
+        ba = p;
+        bb = j;
       }
     } else if (idx < 2 * nx) {
       int k = idx - nx;
       int f = k / N, i = k - f * N;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        UL[v] = R.XY(p, 1, 1, v, f, i + 1);
-        UR[v] = R.XY(p, 1, 0, v, f + 1, i + 1);
-      }
-      st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) R.F2y(p, v, f, i) = F[v];
+      d = 1;
+      pl = &R.XY(p, 1, 1, 0, f, i + 1);
+      pr = &R.XY(p, 1, 0, 0, f + 1, i + 1);
+      pf = &R.F2y(p, 0, f, i);
+      fs = (N + 1) * N;
       if (f == 0 || f == N) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) C.store_flux(f == 0 ? 2 : 3, v, p, i, F[v]);
+        bface = f == 0 ? 2 : 3;
+        ba = p;
+        bb = i;
       }
     } else {
       int k = idx - 2 * nx;
       int j = k / N, i = k - j * N;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        UL[v] = R.Zs(p - 1, 1, v, j + 1, i + 1);
-        UR[v] = R.Zs(p, 0, v, j + 1, i + 1);
-      }
-      st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) R.F2z(p, v, j, i) = F[v];
+      d = 2;
+      pl = &R.Zs(p - 1, 1, 0, j + 1, i + 1);
+      pr = &R.Zs(p, 0, 0, j + 1, i + 1);
+      pf = &R.F2z(p, 0, j, i);
+      fs = N * N;
       if (p == 0 || p == N) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) C.store_flux(p == 0 ? 4 : 5, v, j, i, F[v]);
+        bface = p == 0 ? 4 : 5;
+        ba = j;
+        bb = i;
       }
+    }
+    T UL[5], UR[5], F[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      UL[v] = pl[v * LL];
+      UR[v] = pr[v * LL];
+    }
+    st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
+    if (bface >= 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) C.store_flux(bface, v, ba, bb, F[v]);
     }
   }
   return st;

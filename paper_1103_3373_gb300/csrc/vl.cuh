@@ -80,41 +80,44 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
       const int nx = xy ? LH * (LH + 1) : 0;
       const int nz = pA >= -1 - S_ ? LH * LH : 0;
       const int cnt = 2 * nx + nz;
+      constexpr int PLU = LU * LU;
       for (int idx = tid; idx < cnt; idx += nthr) {
-        T UL[5], UR[5], F[5];
+        const T *pl, *pr;
+        T* pf;
+        int d, fs;
         if (idx < nx) {
           int jj = idx / (LH + 1), f = idx - jj * (LH + 1);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = Ur(pA, v, jj + 1, f);
-            UR[v] = Ur(pA, v, jj + 1, f + 1);
-          }
-          st |= riemann<T, MIXED, RS, 0>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F1.x(pA, v, jj, f) = F[v];
+          d = 0;
+          pl = &Ur(pA, 0, jj + 1, f);
+          pr = &Ur(pA, 0, jj + 1, f + 1);
+          pf = &F1.x(pA, 0, jj, f);
+          fs = LH * (LH + 1);
         } else if (idx < 2 * nx) {
           int k = idx - nx;
           int f = k / LH, ii = k - f * LH;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = Ur(pA, v, f, ii + 1);
-            UR[v] = Ur(pA, v, f + 1, ii + 1);
-          }
-          st |= riemann<T, MIXED, RS, 1>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F1.y(pA, v, f, ii) = F[v];
+          d = 1;
+          pl = &Ur(pA, 0, f, ii + 1);
+          pr = &Ur(pA, 0, f + 1, ii + 1);
+          pf = &F1.y(pA, 0, f, ii);
+          fs = (LH + 1) * LH;
         } else {
           int k = idx - 2 * nx;
           int jj = k / LH, ii = k - jj * LH;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            UL[v] = Ur(pA - 1, v, jj + 1, ii + 1);
-            UR[v] = Ur(pA, v, jj + 1, ii + 1);
-          }
-          st |= riemann<T, MIXED, RS, 2>(UL, UR, o, F);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F1.z(pA, v, jj, ii) = F[v];
+          d = 2;
+          pl = &Ur(pA - 1, 0, jj + 1, ii + 1);
+          pr = &Ur(pA, 0, jj + 1, ii + 1);
+          pf = &F1.z(pA, 0, jj, ii);
+          fs = LH * LH;
         }
+        T UL[5], UR[5], F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          UL[v] = pl[v * PLU];
+          UR[v] = pr[v * PLU];
+        }
+        st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
       }
     }
     __syncthreads();

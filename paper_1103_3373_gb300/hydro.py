@@ -20,7 +20,8 @@ RS_EXACT, RS_HLLE, RS_HLLC, RS_ROE = 0, 1, 2, 3
 FP64, FP32, FP32_MIXED = 0, 1, 2
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 OK, EINVAL, EGHOST, EUNSUPPORTED, ECUDA, EWORKSPACE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6
-NOALLOC_MAX_PARTIALS, NOALLOC_CELLS_PER_CTA = 8192, 16384
+NOALLOC_MAX_PARTIALS, NOALLOC_CELLS_PER_CTA = 8192, 65536
+NOALLOC_MAX_CELLS = (NOALLOC_MAX_PARTIALS // 3) * NOALLOC_CELLS_PER_CTA
 ST_ROE_FALLBACK, ST_NEG_DENS, ST_NEG_PRES, ST_NAN, ST_EXACT_FAIL = 1, 2, 4, 8, 16
 ST_ERROR_MASK = ST_NEG_DENS | ST_NEG_PRES | ST_NAN | ST_EXACT_FAIL
 MAX_LEVELS = 32
@@ -286,7 +287,7 @@ def hydro_cfl_dt_noalloc(U, dx, cfl, dt_out, gamma=1.4, dens_floor=0.0, pres_flo
                          smax_out=None, stream=None):
     """hydro_cfl_dt without a workspace: for callers that cannot allocate
     device memory (its scratch is a fixed static device array; at most
-    NOALLOC_MAX_PARTIALS * NOALLOC_CELLS_PER_CTA cells per call)."""
+    NOALLOC_MAX_CELLS cells per call)."""
     dt = _storage_dtype(precision)
     G, gs, vs, cells = _red_layout(U)
     dxa = (ctypes.c_double * 3)(*[float(a) for a in dx])

@@ -71,6 +71,18 @@ class UniformBox:
     def state(self):
         return self.a
 
+    def tune(self, verbose=False):
+        """Autotune the launch shape of this box's step on its own data."""
+        from . import autotune
+        torch = self.torch
+        torch.cuda.synchronize()
+        best = autotune.tune(self.p, lambda p: H.hydro_advance_uniform(p, self.a, self.b, bc=self.bc, flux=self.flux,
+                                                                       status=self.status, N=self.N, stream=None),
+                             tag="uniform", verbose=verbose)
+        nws = H.hydro_workspace_bytes(self.p, self.N)
+        self.p.workspace = torch.empty(nws, dtype=torch.uint8, device=self.dev) if nws else None
+        return best
+
 
 class HostBoxStepper:
     """End-to-end form of UniformBox.step for a caller that keeps its data on
@@ -115,3 +127,88 @@ def capture_graph(fn, stream=None, warmup=1):
 
 def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else float("nan")
+
+
+class LevelBatch:
+    """Uneven per-AMR-level lists of halo-prepared groups advanced by ONE
+    persistent launch (hydro_advance_levels), each level with its own dx and
+    its own device dt from its own CFL reduction (Sec. 4.3 per level).
+
+    step() = one CFL reduction per level + the batched launch; it takes no
+    host synchronisation and can be captured once into a CUDA graph
+    (capture()) and replayed.  step_per_level() is the plain form: one
+    hydro_advance launch per level.
+    """
+
+    def __init__(self, levels, params: H.Params, cfl=0.4, N=16, ghost=3, device="cuda:0", stream=None,
+                 store_flux=True):
+        torch = _torch()
+        self.torch = torch
+        self.dev = torch.device(device)
+        self.p = params
+        self.cfl = cfl
+        self.N, self.ghost = N, ghost
+        dt = torch.float64 if params.precision == H.FP64 else torch.float32
+        self.U_in, self.U_out, self.flux, self.status, self.dts, self.dx = [], [], [], [], [], []
+        for lv in levels:
+            U = torch.as_tensor(lv["U"], dtype=dt).to(self.dev).contiguous()
+            G = U.shape[0]
+            self.U_in.append(U)
+            self.U_out.append(torch.empty((G, 5, N, N, N), dtype=dt, device=self.dev))
+            self.flux.append(torch.empty((G, 6, 5, N, N), dtype=dt, device=self.dev) if store_flux else None)
+            self.status.append(torch.zeros(G, dtype=torch.int32, device=self.dev))
+            self.dts.append(torch.zeros(1, dtype=torch.float64, device=self.dev))
+            self.dx.append((lv["dx"],) * 3)
+        self.cells = sum(u.shape[0] for u in self.U_in) * N ** 3
+        self.red_ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=self.dev)
+        self.stream = stream
+        self._alloc_ws()
+        self.graph = None
+
+    def _alloc_ws(self):
+        nws = H.hydro_workspace_bytes(self.p, self.N)
+        self.p.workspace = self.torch.empty(nws, dtype=self.torch.uint8, device=self.dev) if nws else None
+        self.entries = [H.Level(U_in=self.U_in[l], U_out=self.U_out[l], flux=self.flux[l], status=self.status[l],
+                                dx=self.dx[l], dt_dev=self.dts[l], mode=0) for l in range(len(self.U_in))]
+        self.carray = H.make_levels(self.entries, self.p.precision)
+
+    def reduce_dt(self, stream=None):
+        s = stream if stream is not None else self.stream
+        for l, U in enumerate(self.U_in):
+            H.hydro_cfl_dt(U, self.dx[l], self.cfl, self.dts[l], self.red_ws, gamma=self.p.gamma,
+                           dens_floor=self.p.dens_floor, pres_floor=self.p.pres_floor, precision=self.p.precision,
+                           stream=s)
+
+    def advance_batched(self, stream=None):
+        s = stream if stream is not None else self.stream
+        H.hydro_advance_levels(self.p, self.entries, N=self.N, ghost=self.ghost, stream=s, _carray=self.carray)
+
+    def step(self, stream=None):
+        self.reduce_dt(stream)
+        self.advance_batched(stream)
+
+    def step_per_level(self, stream=None):
+        s = stream if stream is not None else self.stream
+        self.reduce_dt(s)
+        for l in range(len(self.U_in)):
+            self.p.dx, self.p.dt_dev = self.dx[l], self.dts[l]
+            H.hydro_advance(self.p, self.U_in[l], self.U_out[l], self.flux[l], self.status[l], N=self.N,
+                            ghost=self.ghost, stream=s)
+        self.p.dt_dev = None
+
+    def tune(self, verbose=False):
+        from . import autotune
+        self.torch.cuda.synchronize()
+        best = autotune.tune(self.p, lambda p: H.hydro_advance_levels(
+            p, self.entries, N=self.N, ghost=self.ghost, stream=None,
+            _carray=H.make_levels(self.entries, p.precision)), tag="levels", verbose=verbose)
+        self._alloc_ws()
+        return best
+
+    def capture(self):
+        """Capture step() into a CUDA graph (replay with replay())."""
+        self.graph = capture_graph(lambda: self.step(self.torch.cuda.current_stream()))
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()

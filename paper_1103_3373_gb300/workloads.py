@@ -158,3 +158,77 @@ def poisson_arrivals(rate=200.0, n=2000, seed=6):
     seeds = rng.integers(0, 2 ** 31 - 1, n)
     return [dict(t=float(t[i]), n=int(sizes[i]), mach=float(mach[i]), steps=int(steps[i]), seed=int(seeds[i]))
             for i in range(n)]
+
+
+def _pad_periodic(U, g):
+    return np.pad(U, ((0, 0), (g, g), (g, g), (g, g)), mode="wrap")
+
+
+def _grad_score(rho):
+    """max over cells of |grad rho| / rho (central differences, unit spacing)."""
+    gx = 0.5 * (rho[..., 2:] - rho[..., :-2])[1:-1, 1:-1]
+    gy = 0.5 * (rho[:, 2:, :] - rho[:, :-2, :])[1:-1, :, 1:-1]
+    gz = 0.5 * (rho[2:, :, :] - rho[:-2, :, :])[:, 1:-1, 1:-1]
+    return np.sqrt(gx * gx + gy * gy + gz * gz) / rho[1:-1, 1:-1, 1:-1]
+
+
+def amr_levels(counts=(4096, 2500, 1500, 800), n0=128, seed=5, N=16, g=3, mach=1.5, gamma=1.4, threshold=0.3,
+               dtype=np.float32):
+    """AMR-shaped batch: per level a list of halo-prepared patch groups [G,5,M,M,M].
+
+    Level 0 tiles a periodic lognormal root of n0^3 cells (seed `seed`); the
+    stated per-level counts are authoritative, so the root's groups are
+    repeated on seeded periodic shifts of the root until count[0] is reached.
+    Level l+1 refines the groups of level l that score highest in
+    max |grad rho|/rho (cells above `threshold` flag a group); each refined
+    group yields its 8 children (16^3 cells at twice the resolution) by
+    trilinear interpolation of the parent's halo-padded data, with a seeded
+    1% k^-3 density perturbation.  Ghost zones are prepared (filled from the
+    parent), as the AMR ghost interpolation itself is not part of this path.
+    Returns a list of dicts {U: groups, dx, score, flagged_fraction}.
+    """
+    from scipy import ndimage
+    rng = np.random.default_rng(seed)
+    root = lognormal(n0, seed=seed, mach=mach, gamma=gamma)
+    M = N + 2 * g
+    levels = []
+    # level 0
+    groups, scores = [], []
+    shift = np.zeros(3, dtype=int)
+    while len(groups) < counts[0]:
+        f = np.roll(root, tuple(-shift[::-1]), axis=(1, 2, 3))
+        fp = _pad_periodic(f, g)
+        sc = _grad_score(fp[0])
+        for (x0, y0, z0) in group_origins(n0, n0, n0, N):
+            if len(groups) >= counts[0]:
+                break
+            groups.append(fp[:, z0:z0 + M, y0:y0 + M, x0:x0 + M])
+            scores.append(sc[z0:z0 + M - 2, y0:y0 + M - 2, x0:x0 + M - 2].max())
+        shift = rng.integers(0, n0, 3)
+    U0 = np.stack(groups).astype(dtype)
+    levels.append({"U": U0, "dx": 1.0 / n0, "score": np.asarray(scores),
+                   "flagged_fraction": float(np.mean(np.asarray(scores) > threshold))})
+    # refined levels
+    for l in range(1, len(counts)):
+        prev = levels[-1]
+        need = int(np.ceil(counts[l] / 8))
+        order = np.argsort(-prev["score"], kind="stable")
+        parents = [order[k % len(order)] for k in range(need)]
+        kids, ksc = [], []
+        for pi in parents:
+            P = prev["U"][pi].astype(np.float64)
+            fine = np.stack([ndimage.zoom(P[v], 2, order=1, mode="nearest", grid_mode=True) for v in range(5)])
+            pert = gaussian_field(2 * M, int(rng.integers(0, 2 ** 31 - 1)))
+            fine[0] *= 1.0 + 0.01 * pert
+            sc = _grad_score(fine[0])
+            for cz in (0, 1):
+                for cy in (0, 1):
+                    for cx in (0, 1):
+                        a = (N * cz + 2 * g - g, N * cy + 2 * g - g, N * cx + 2 * g - g)
+                        kids.append(fine[:, a[0]:a[0] + M, a[1]:a[1] + M, a[2]:a[2] + M])
+                        ksc.append(sc[a[0]:a[0] + M - 2, a[1]:a[1] + M - 2, a[2]:a[2] + M - 2].max())
+        Ul = np.stack(kids[:counts[l]]).astype(dtype)
+        sl = np.asarray(ksc[:counts[l]])
+        levels.append({"U": Ul, "dx": prev["dx"] / 2.0, "score": sl,
+                       "flagged_fraction": float(np.mean(sl > threshold))})
+    return levels

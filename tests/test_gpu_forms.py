@@ -1,0 +1,116 @@
+"""GPU tests of the batched and serving forms (through the C ABI).
+
+* AMR-shaped batch: uneven per-level group lists advanced by one persistent
+  launch equal one launch per level byte for byte; the CUDA-graph replay of a
+  step equals the eager step; sampled groups of every level match the oracle
+  with that level's dx and dt.
+* Autotuner: picks a launch shape that runs and gives the same bytes.
+* Serving: every request's result is the same alone and in the mix (and
+  equal to stepping its box on its own with UniformBox).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1103_3373_gb300 import hydro as H
+from paper_1103_3373_gb300 import runtime as RT
+from paper_1103_3373_gb300 import serving as SV
+from paper_1103_3373_gb300 import workloads as W
+from tests.gpu_common import TOL_FP32, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small_levels():
+    return W.amr_levels(counts=(40, 24, 16, 8), n0=32, seed=5)
+
+
+def _params(prec=H.FP32):
+    return H.Params(scheme=H.CTU, recon=H.PPM, riemann=H.RS_ROE, precision=prec, dens_floor=1e-6, pres_floor=1e-6)
+
+
+def test_levels_batched_graph_and_oracle(small_levels):
+    import torch
+    lb = RT.LevelBatch(small_levels, _params())
+    lb.step()
+    torch.cuda.synchronize()
+    batched = [u.clone() for u in lb.U_out]
+    fl = [f.clone() for f in lb.flux]
+    dts = [d.item() for d in lb.dts]
+    for u in lb.U_out:
+        u.fill_(float("nan"))
+    lb.step_per_level()
+    torch.cuda.synchronize()
+    for a, b in zip(batched, lb.U_out):
+        assert torch.equal(a, b)
+    for u in lb.U_out:
+        u.fill_(float("nan"))
+    lb.capture()
+    lb.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(batched, lb.U_out):
+        assert torch.equal(a, b)
+    for a, b in zip(fl, lb.flux):
+        assert torch.equal(a, b)
+    # sampled groups of every level against the oracle (same dt, dx)
+    for l, lv in enumerate(small_levels):
+        U = lv["U"].astype(np.float64)
+        dx = (lv["dx"],) * 3
+        assert dts[l] == pytest.approx(O.cfl_dt(U, dx, 0.4, 1.4, 1e-6, 1e-6), rel=1e-6)  # FP32 per-cell speeds
+        P = O.Params(scheme=O.CTU, recon=O.PPM, riemann=O.ROE, dt=dts[l], dx=dx, dens_floor=1e-6, pres_floor=1e-6)
+        pick = [0, U.shape[0] - 1]
+        ref, ref_flux, _ = O.advance(P, U[pick], 16)
+        got = batched[l][pick].double().cpu().numpy()
+        assert rel_l1(got, ref) <= TOL_FP32
+        assert rel_l1(fl[l][pick].double().cpu().numpy().reshape(-1, 5, 256), ref_flux.reshape(-1, 5, 256)) <= TOL_FP32
+
+
+def test_autotune_picks_a_working_shape(small_levels):
+    import torch
+    from paper_1103_3373_gb300 import autotune
+    lb = RT.LevelBatch(small_levels, _params())
+    lb.step()
+    torch.cuda.synchronize()
+    ref = [u.clone() for u in lb.U_out]
+    best = lb.tune()
+    assert 128 <= best["block_threads"] <= H.hydro_max_block_threads(lb.p)
+    lb.step()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, lb.U_out):
+        assert torch.equal(a, b)
+    # cached: a second call returns the same choice without re-timing
+    again = autotune.tune(lb.p, lambda p: None, tag="levels")
+    assert (again["block_threads"], again["grid_ctas"]) == (best["block_threads"], best["grid_ctas"])
+
+
+def test_serving_results_same_alone_and_in_the_mix():
+    import torch
+    reqs = [SV.Request(rid=i, t_arrive=0.0, n=n, mach=m, steps=s, seed=sd)
+            for i, (n, m, s, sd) in enumerate([(32, 0.7, 3, 11), (64, 2.0, 5, 12), (32, 2.8, 7, 13),
+                                                (64, 1.1, 2, 14), (32, 1.5, 4, 15)])]
+    mixed = SV.ServingEngine(_params(), sizes=(32, 64), keep_results=True)
+    summ = mixed.run([SV.Request(**{k: getattr(r, k) for k in ("rid", "t_arrive", "n", "mach", "steps", "seed")})
+                      for r in reqs], realtime=False)
+    assert summ["requests"] == len(reqs) and summ["max_active"] == len(reqs)
+    res_mix = {r.rid: r.result for r in mixed.done}
+    for r in reqs:
+        alone = SV.ServingEngine(_params(), sizes=(32, 64), keep_results=True)
+        alone.run([SV.Request(**{k: getattr(r, k) for k in ("rid", "t_arrive", "n", "mach", "steps", "seed")})],
+                  realtime=False)
+        assert torch.equal(alone.done[0].result, res_mix[r.rid])
+        # and the same as stepping the box by itself
+        U0 = alone.states.make(r.n, r.mach, r.seed).double().cpu().numpy()
+        box = RT.UniformBox(U0, _params(), cfl=0.4)
+        for _ in range(r.steps):
+            box.step()
+        torch.cuda.synchronize()
+        assert torch.equal(box.state().cpu(), res_mix[r.rid])
+
+
+def test_serving_admission_respects_budget():
+    reqs = [SV.Request(rid=i, t_arrive=0.0, n=64, mach=1.0, steps=2, seed=i) for i in range(6)]
+    eng = SV.ServingEngine(_params(), sizes=(64,), budget_bytes=3 * (2 * 5 * 64 ** 3 * 4 + 64 * 4 + 8))
+    summ = eng.run(reqs, realtime=False)
+    assert summ["requests"] == 6
+    assert summ["max_active"] == 3

@@ -61,7 +61,7 @@ def test_noalloc_grouped_layout_and_size_limit():
     # one cell more than the static scratch covers: refused, nothing launched
     L = H.library()
     dxa = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
-    too_many = H.NOALLOC_MAX_PARTIALS * H.NOALLOC_CELLS_PER_CTA + 1
+    too_many = H.NOALLOC_MAX_CELLS + 1
     rc = L.hydro_cfl_dt_noalloc(Ut.data_ptr(), 1, 5 * too_many, too_many, too_many, H.FP32, 1.4, 0.0, 0.0, dxa, 0.4,
                                 dt.data_ptr(), None, torch.cuda.current_stream().cuda_stream)
     assert rc == H.ETOOBIG
