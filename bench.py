@@ -307,6 +307,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mixed / VL detail lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--quick", action="store_true", help="main line only (no extra, cpu_baseline or e2e legs)")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="use this many threads per CTA for the main line instead of autotuning")
     args = ap.parse_args()
     if args.quick:
         args.no_extra = args.no_cpu = True
@@ -338,7 +340,11 @@ def main():
     cells = N_BOX ** 3
     stream = torch.cuda.Stream(device=dev)
     box = RT.UniformBox(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev, stream=stream)
-    tuned = box.tune()
+    if args.block_threads:
+        box.p.block_threads = args.block_threads
+        tuned = {"block_threads": args.block_threads, "grid_ctas": 0, "fixed": True}
+    else:
+        tuned = box.tune()
     box.compute_dt()
     sampler = ClockSampler(local)
     if dist:

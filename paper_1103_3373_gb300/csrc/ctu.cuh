@@ -63,73 +63,37 @@ template <class T, int N, int S> struct CtuF1 {
   }
 };
 
-// Step (1) for one cell along direction D: reconstruction of the primitive
-// ring around (jj, ii) of plane p, characteristic tracing to t + dt/2, and the
-// two traced face states as conserved variables (Ul: left face, Ur: right).
-template <int D, int REC, int LIM, class T, class WRing>
-__device__ __forceinline__ void trace_cell(const WRing& Wr, int p, int jj, int ii, const Opts<T>& o, T dtdx, T Ul[5],
-                                           T Ur[5]) {
-  constexpr int S_ = REC == PPM ? 2 : 1;
-  T w[5][5], WLf[5], WRf[5], dW[5], W0[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-#pragma unroll
-    for (int o2 = -S_; o2 <= S_; ++o2) {
-      if (D == 0) w[v][o2 + 2] = Wr(p, v, jj + S_, ii + S_ + o2);
-      else if (D == 1) w[v][o2 + 2] = Wr(p, v, jj + S_ + o2, ii + S_);
-      else w[v][o2 + 2] = Wr(p + o2, v, jj + S_, ii + S_);
-    }
-    W0[v] = w[v][2];
-  }
-  recon5<REC, LIM>(w, o, WLf, WRf, dW);
-  T w0l[5], a[5], b[5], tl[5], tr[5];
-  rot_in<D>(W0, w0l);
-  if (REC == PPM) {
-    rot_in<D>(WLf, a);
-    rot_in<D>(WRf, b);
-    trace_ppm(w0l, a, b, dtdx, o.gas, tl, tr);
-  } else {
-    rot_in<D>(dW, a);
-    trace_plm(w0l, a, dtdx, o.gas, tl, tr);
-  }
-  T wg[5];
-  rot_out<D>(tl, wg);
-  cons(wg, Ul, o.gas);
-  rot_out<D>(tr, wg);
-  cons(wg, Ur, o.gas);
-}
-
-// The same for a direction known only at run time (one inlined copy).
+// Step (1) for one cell along direction d (known at run time; one inlined
+// copy serves all three): reconstruction of the primitive ring around
+// (jj, ii) of plane p, characteristic tracing to t + dt/2.  The
+// rotation into the local frame is folded into the shared-memory addressing;
+// the traced states come back in the local frame (Ul, Ur conserved, normal
+// momentum first).
 template <int REC, int LIM, class T, class WRing>
-__device__ __forceinline__ void trace_cell_rt(const WRing& Wr, int p, int jj, int ii, int d, const Opts<T>& o, T dtdx,
-                                              T Ul[5], T Ur[5]) {
+__device__ __forceinline__ void trace_cell_rt(const WRing& Wr, int p, int jj, int ii, int d, const LocalComps& lc,
+                                              const Opts<T>& o, T dtdx, T Ul[5], T Ur[5]) {
   constexpr int S_ = REC == PPM ? 2 : 1;
+  constexpr int VS = WRing::PL / 5;  // variable stride of a W plane
   const int sx = d == 0, sy = d == 1, sz = d == 2;
   T w[5][5], WLf[5], WRf[5], dW[5], W0[5];
 #pragma unroll
   for (int o2 = -S_; o2 <= S_; ++o2) {
     const T* base = &Wr(p + sz * o2, 0, jj + S_ + sy * o2, ii + S_ + sx * o2);
+    T a[5];
+    load_local(base, VS, lc, a);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) w[v][o2 + 2] = base[v * WRing::PL / 5];
+    for (int v = 0; v < 5; ++v) w[v][o2 + 2] = a[v];
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) W0[v] = w[v][2];
   recon5<REC, LIM>(w, o, WLf, WRf, dW);
-  T w0l[5], a[5], b[5], tl[5], tr[5];
-  rot_in_rt(W0, w0l, d);
-  if (REC == PPM) {
-    rot_in_rt(WLf, a, d);
-    rot_in_rt(WRf, b, d);
-    trace_ppm(w0l, a, b, dtdx, o.gas, tl, tr);
-  } else {
-    rot_in_rt(dW, a, d);
-    trace_plm(w0l, a, dtdx, o.gas, tl, tr);
-  }
-  T wg[5];
-  rot_out_rt(tl, wg, d);
-  cons(wg, Ul, o.gas);
-  rot_out_rt(tr, wg, d);
-  cons(wg, Ur, o.gas);
+  T tl[5], tr[5];
+  if (REC == PPM)
+    trace_ppm(W0, WLf, WRf, dtdx, o.gas, tl, tr);
+  else
+    trace_plm(W0, dW, dtdx, o.gas, tl, tr);
+  cons_local(tl, d, o.gas, Ul);
+  cons_local(tr, d, o.gas, Ur);
 }
 
 // Transverse flux-gradient correction (step (3)) of one face state:
@@ -181,15 +145,13 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           int rem = k - d * LL;
           int jj = rem / L, ii = rem - jj * L;
           T Ul[5], Ur[5];
-          trace_cell_rt<REC, LIM>(Wr, q, jj, ii, d, o, d == 0 ? C.dtdx[0] : (d == 1 ? C.dtdx[1] : C.dtdx[2]), Ul,
-                                  Ur);
+          const LocalComps lc(d);
+          trace_cell_rt<REC, LIM>(Wr, q, jj, ii, d, lc, o, d == 0 ? C.dtdx[0] : (d == 1 ? C.dtdx[1] : C.dtdx[2]),
+                                  Ul, Ur);
           T* dl = d < 2 ? &R.XY(q, d, 0, 0, jj, ii) : &R.Zs(q, 0, 0, jj, ii);
           T* dr = d < 2 ? &R.XY(q, d, 1, 0, jj, ii) : &R.Zs(q, 1, 0, jj, ii);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            dl[v * LL] = Ul[v];
-            dr[v * LL] = Ur[v];
-          }
+          store_local(dl, LL, lc, Ul);
+          store_local(dr, LL, lc, Ur);
         }
       }
       for (int k = tid; k < nf; k += nthr) {
@@ -241,15 +203,12 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           pf = &F1.z(q, 0, jj, ii);
           fs = LL;
         }
+        const LocalComps lc(d);
         T UL[5], UR[5], F[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          UL[v] = pl[v * LL];
-          UR[v] = pr[v * LL];
-        }
-        st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
+        load_local(pl, LL, lc, UL);
+        load_local(pr, LL, lc, UR);
+        st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+        store_local(pf, fs, lc, F);
       }
     }
     __syncthreads();
@@ -263,9 +222,14 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
       const int na = (pa <= N + S_) ? LW * LW : 0;
       // the next plane's global loads are issued first and converted after
       // the Riemann work, so their latency hides behind it
+      // the load items go to the threads with the fewest face items: thread t
+      // has ceil((ne - t) / nthr) of them, one more below ne % nthr
+      const int aw0 = ne % nthr;
+      const int naw = nthr - aw0;
+      const int atid = tid - aw0;
       T Ua0[5];
-      if (tid < na) {
-        int jj = tid / LW, ii = tid - jj * LW;
+      if (atid >= 0 && atid < na) {
+        int jj = atid / LW, ii = atid - jj * LW;
         C.load5(ii - 1 - S_, jj - 1 - S_, pa, Ua0);
       }
       for (int idx = tid; idx < ne; idx += nthr) {
@@ -351,24 +315,26 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
         // variable strides of the stage-1 flux arrays used for e1 and e2
         const int s1 = d == 0 ? (N + 1) * L : L * (N + 1);
         const int s2 = d == 2 ? (N + 1) * L : LL;
+        const LocalComps lc(d);
+        const int gv[5] = {0, lc.c1, lc.c2, lc.c3, 4};  // global variable of each local slot
         T UL[5], UR[5], F[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          UL[v] = correct(sl[v * LL], g1, a1p[v * s1], a1m[v * s1], g2, a2p[v * s2], a2m[v * s2]);
-          UR[v] = correct(sr[v * LL], g1, b1p[v * s1], b1m[v * s1], g2, b2p[v * s2], b2m[v * s2]);
+        for (int k = 0; k < 5; ++k) {
+          const int v = gv[k];
+          UL[k] = correct(sl[v * LL], g1, a1p[v * s1], a1m[v * s1], g2, a2p[v * s2], a2m[v * s2]);
+          UR[k] = correct(sr[v * LL], g1, b1p[v * s1], b1m[v * s1], g2, b2p[v * s2], b2m[v * s2]);
         }
-        st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
+        st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+        store_local(pf, fs, lc, F);
         if (bface >= 0) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) C.store_flux(bface, v, ba, bb, F[v]);
+          for (int k = 0; k < 5; ++k) C.store_flux(bface, gv[k], ba, bb, F[k]);
         }
       }
-      for (int k = tid; k < na; k += nthr) {
+      for (int k = atid; atid >= 0 && k < na; k += naw) {
         int jj = k / LW, ii = k - jj * LW;
         T U[5], W[5];
-        if (k == tid) {
+        if (k == atid) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) U[v] = Ua0[v];
         } else {
@@ -386,8 +352,8 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
 
 template <class T, class S, bool MIXED, int RS, int REC, int N>
 __device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
-  if (o.limiter == LIM_MINMOD)
-    ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD, N>(C, o, ring, st_sh);
+  if (o.limiter == LIM_MINMOD && o.theta == T(1))
+    ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD1, N>(C, o, ring, st_sh);
   else
     ctu_group_impl<T, S, MIXED, RS, REC, -1, N>(C, o, ring, st_sh);
 }

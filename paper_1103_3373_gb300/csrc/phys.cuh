@@ -21,6 +21,10 @@ namespace hyd {
 enum { MHM = 0, VL = 1, CTU = 2 };
 enum { PLM = 0, PPM = 1 };
 enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_VANALBADA = 2, LIM_HYBRID = 3 };
+// Internal: generalized minmod with theta = 1, i.e. sign(dL) min(|dL|, |dR|)
+// (equal, value for value, to the three-term form: |dC| >= min(|dL|, |dR|)
+// when dL dR > 0, also after rounding).
+constexpr int LIM_MINMOD1 = 4;
 enum { RS_EXACT = 0, RS_HLLE = 1, RS_HLLC = 2, RS_ROE = 3 };
 enum { P_FP64 = 0, P_FP32 = 1, P_MIXED = 2 };
 
@@ -76,24 +80,6 @@ template <int D, class T> __device__ __forceinline__ void rot_out(const T b[5], 
   a[Dir<D>::n] = b[1];
   a[Dir<D>::t1] = b[2];
   a[Dir<D>::t2] = b[3];
-  a[4] = b[4];
-}
-
-// Run-time direction: the same permutations written as selects, so one
-// inlined copy of a solver serves all three directions (the kernels stay
-// small enough for the instruction caches).
-template <class T> __device__ __forceinline__ void rot_in_rt(const T a[5], T b[5], int d) {
-  b[0] = a[0];
-  b[1] = d == 0 ? a[1] : (d == 1 ? a[2] : a[3]);
-  b[2] = d == 0 ? a[2] : (d == 1 ? a[3] : a[1]);
-  b[3] = d == 0 ? a[3] : (d == 1 ? a[1] : a[2]);
-  b[4] = a[4];
-}
-template <class T> __device__ __forceinline__ void rot_out_rt(const T b[5], T a[5], int d) {
-  a[0] = b[0];
-  a[1] = d == 0 ? b[1] : (d == 1 ? b[3] : b[2]);
-  a[2] = d == 0 ? b[2] : (d == 1 ? b[1] : b[3]);
-  a[3] = d == 0 ? b[3] : (d == 1 ? b[2] : b[1]);
   a[4] = b[4];
 }
 
@@ -156,6 +142,13 @@ template <class T> __device__ __forceinline__ T csound(T rho, T p, const Gas<T>&
 // Evaluated without branches on the data (selects), so neighbouring cells of
 // a warp never diverge; the selected values are those of the formulas above.
 template <int LIM = -1, class T> __device__ __forceinline__ T slope(int lim, T theta, T dL, T dR) {
+  if (LIM == LIM_MINMOD1) {
+    T prod = dL * dR;
+    T a = absv(dL), b = absv(dR);
+    T m = b < a ? b : a;
+    T r = dL > T(0) ? m : -m;
+    return prod > T(0) ? r : T(0);
+  }
   if (LIM >= 0) lim = LIM;
   T prod = dL * dR;
   T dC = T(0.5) * (dL + dR);
@@ -641,14 +634,10 @@ template <class T> __device__ __forceinline__ bool roe(const Side<T>& L, const S
   return true;
 }
 
-// Riemann flux along D for global-frame conserved states; returns status
-// bits.  Where Roe fails, the fallback of Sec. 2 (HLLE / HLLC inline, the
-// exact solver out of line) gives the flux.
-template <class T, bool MIXED, int RS, int D>
-__device__ __forceinline__ unsigned riemann(const T ULg[5], const T URg[5], const Opts<T>& o, T Fg[5]) {
-  T ul[5], ur[5], F[5];
-  rot_in<D>(ULg, ul);
-  rot_in<D>(URg, ur);
+// Riemann flux in the local frame (states and flux already ordered normal
+// first); returns status bits.
+template <class T, bool MIXED, int RS>
+__device__ __forceinline__ unsigned riemann_local(const T ul[5], const T ur[5], const Opts<T>& o, T F[5]) {
   Side<T> L, R;
   mkside<T, MIXED>(ul, o.gas, L);
   mkside<T, MIXED>(ur, o.gas, R);
@@ -670,39 +659,48 @@ __device__ __forceinline__ unsigned riemann(const T ULg[5], const T URg[5], cons
   } else {
     st = exact_call(L, R, o.gas, F);
   }
-  rot_out<D>(F, Fg);
   return st;
 }
 
-// Same as riemann<..., D> for a direction known only at run time.
-template <class T, bool MIXED, int RS>
-__device__ __forceinline__ unsigned riemann_rt(int d, const T ULg[5], const T URg[5], const Opts<T>& o, T Fg[5]) {
-  T ul[5], ur[5], F[5];
-  rot_in_rt(ULg, ul, d);
-  rot_in_rt(URg, ur, d);
-  Side<T> L, R;
-  mkside<T, MIXED>(ul, o.gas, L);
-  mkside<T, MIXED>(ur, o.gas, R);
-  unsigned st = 0;
-  if (RS == RS_ROE) {
-    if (!roe(L, R, o.gas, F)) {
-      st = ST_ROE_FALLBACK;
-      if (o.fallback == RS_HLLC)
-        hllc(L, R, o.gas, F);
-      else if (o.fallback == RS_EXACT)
-        st |= exact_call(L, R, o.gas, F);
-      else
-        hlle(L, R, o.gas, F);
-    }
-  } else if (RS == RS_HLLC) {
-    hllc(L, R, o.gas, F);
-  } else if (RS == RS_HLLE) {
-    hlle(L, R, o.gas, F);
-  } else {
-    st = exact_call(L, R, o.gas, F);
-  }
-  rot_out_rt(F, Fg, d);
-  return st;
+// Global component of the local momentum components for direction d:
+// local 1, 2, 3 = global 1 + d, 1 + (d+1)%3, 1 + (d+2)%3.
+struct LocalComps {
+  int c1, c2, c3;
+  __device__ __forceinline__ explicit LocalComps(int d)
+      : c1(1 + d), c2(d == 2 ? 1 : d + 2), c3(d == 0 ? 3 : d) {}
+};
+
+// Load / store a 5-vector in the local frame of direction d from / to memory
+// holding it in the global frame with element stride s.
+template <class T>
+__device__ __forceinline__ void load_local(const T* p, int s, const LocalComps& lc, T a[5]) {
+  a[0] = p[0];
+  a[1] = p[lc.c1 * s];
+  a[2] = p[lc.c2 * s];
+  a[3] = p[lc.c3 * s];
+  a[4] = p[4 * s];
+}
+template <class T>
+__device__ __forceinline__ void store_local(T* p, int s, const LocalComps& lc, const T a[5]) {
+  p[0] = a[0];
+  p[lc.c1 * s] = a[1];
+  p[lc.c2 * s] = a[2];
+  p[lc.c3 * s] = a[3];
+  p[4 * s] = a[4];
+}
+
+// W -> U for a state given in the local frame of direction d, with the
+// kinetic sum taken in the GLOBAL component order (u^2 + v^2) + w^2, so the
+// result equals cons() of the rotated-back state value for value.
+template <class T> __device__ __forceinline__ void cons_local(const T W[5], int d, const Gas<T>& g, T U[5]) {
+  T a = W[1] * W[1], b = W[2] * W[2], c = W[3] * W[3];
+  // global (u, v, w) = (n, t1, t2) for x, (t2, n, t1) for y, (t1, t2, n) for z
+  T ke = d == 0 ? a + b + c : (d == 1 ? c + a + b : b + c + a);
+  U[0] = W[0];
+  U[1] = W[0] * W[1];
+  U[2] = W[0] * W[2];
+  U[3] = W[0] * W[3];
+  U[4] = W[4] / g.gm1 + T(0.5) * W[0] * ke;
 }
 
 }  // namespace hyd

@@ -97,18 +97,16 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
         bb = i;
       }
     }
+    const LocalComps lc(d);
     T UL[5], UR[5], F[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      UL[v] = pl[v * LL];
-      UR[v] = pr[v * LL];
-    }
-    st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
+    load_local(pl, LL, lc, UL);
+    load_local(pr, LL, lc, UR);
+    st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+    store_local(pf, fs, lc, F);
     if (bface >= 0) {
+      const int gv[5] = {0, lc.c1, lc.c2, lc.c3, 4};
 #pragma unroll
-      for (int v = 0; v < 5; ++v) C.store_flux(bface, v, ba, bb, F[v]);
+      for (int k = 0; k < 5; ++k) C.store_flux(bface, gv[k], ba, bb, F[k]);
     }
   }
   return st;

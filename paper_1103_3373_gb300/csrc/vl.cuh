@@ -109,15 +109,12 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
           pf = &F1.z(pA, 0, jj, ii);
           fs = LH * LH;
         }
+        const LocalComps lc(d);
         T UL[5], UR[5], F[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          UL[v] = pl[v * PLU];
-          UR[v] = pr[v * PLU];
-        }
-        st |= riemann_rt<T, MIXED, RS>(d, UL, UR, o, F);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) pf[v * fs] = F[v];
+        load_local(pl, PLU, lc, UL);
+        load_local(pr, PLU, lc, UR);
+        st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+        store_local(pf, fs, lc, F);
       }
     }
     __syncthreads();
