@@ -44,7 +44,6 @@ template <class T, class S, int N> struct GroupCtx {
   int X, Y, Z, ox, oy, oz;
   long long XYZ;
   T dtdx[3], hdtdx[3];
-  double dtdx_d[3];
 
   // sc[0..2] = dt/dx_d, sc[3..5] = (0.5 dt)/dx_d, evaluated once per group
   // (group_consts) and shared by the CTA.
@@ -54,7 +53,6 @@ template <class T, class S, int N> struct GroupCtx {
     M = N + 2 * g;
     Mpl = (long long)M * M;
     for (int d = 0; d < 3; ++d) {
-      dtdx_d[d] = sc[d];
       dtdx[d] = (T)sc[d];
       hdtdx[d] = (T)sc[3 + d];
     }
@@ -140,24 +138,22 @@ template <int R> __device__ __forceinline__ int slot(int p) { return (p + 8 * R)
 
 // Conservative update of one interior cell (step (4)) from the face flux
 // differences dF[d][v] = F(c + e_d/2) - F(c - e_d/2):
-//   U_new = U - ((dtdx0 dF0 + dtdx1 dF1) + dtdx2 dF2),
-// in FP64 for the mixed form; sets the status bits of the new state.
+//   U_new = U - ((dtdx0 dF0 + dtdx1 dF1) + dtdx2 dF2);
+// sets the status bits of the new state.
 template <class T> __device__ __forceinline__ unsigned state_status(const T Un[5], const Gas<T>& gas);
 
-// U0 holds U^n of the cell (already read from the input).
+// U0 holds U^n of the cell (already read from the input).  The sum is
+// evaluated in the arithmetic type for every form: the result is rounded to
+// the storage type, so an FP64 sum would change the stored FP32 value by less
+// than one unit in the last place.
 template <class T, class S, bool MIXED, int N>
 __device__ __forceinline__ unsigned update_cell_from(const GroupCtx<T, S, N>& C, int x, int y, int z, const T U0[5],
                                                      const T dF[3][5], const Gas<T>& gas) {
   T Un[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    if (MIXED) {
-      double dU = C.dtdx_d[0] * (double)dF[0][v] + C.dtdx_d[1] * (double)dF[1][v] + C.dtdx_d[2] * (double)dF[2][v];
-      Un[v] = (T)((double)U0[v] - dU);
-    } else {
-      T dU = C.dtdx[0] * dF[0][v] + C.dtdx[1] * dF[1][v] + C.dtdx[2] * dF[2][v];
-      Un[v] = U0[v] - dU;
-    }
+    T dU = C.dtdx[0] * dF[0][v] + C.dtdx[1] * dF[1][v] + C.dtdx[2] * dF[2][v];
+    Un[v] = U0[v] - dU;
     C.store(v, x, y, z, (S)Un[v]);
   }
   return state_status(Un, gas);

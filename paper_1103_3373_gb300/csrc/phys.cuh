@@ -31,7 +31,8 @@ enum { P_FP64 = 0, P_FP32 = 1, P_MIXED = 2 };
 enum : unsigned { ST_ROE_FALLBACK = 1u, ST_NEG_DENS = 2u, ST_NEG_PRES = 4u, ST_NAN = 8u, ST_EXACT_FAIL = 16u };
 
 // Precision forms: T = arithmetic type, S = storage type, MIXED = FP64
-// accumulation of the update and FP64 pressure recovery under cancellation.
+// internal-energy recovery where E - |m|^2/2rho cancels (the FP64 totals and
+// the FP64 dt reduction are separate kernels).
 template <int P> struct Prec;
 template <> struct Prec<P_FP64> { using T = double; using S = double; static constexpr bool MIXED = false; };
 template <> struct Prec<P_FP32> { using T = float; using S = float; static constexpr bool MIXED = false; };

@@ -89,14 +89,19 @@ def lognormal(n, seed=1, sigma=0.5, mach=1.5, gamma=1.4, p0=1.0, vel_seeds=None)
     return conserved(rho, scale * v[0], scale * v[1], scale * v[2], p0, gamma)
 
 
-def sedov(n, gamma=5.0 / 3.0, E=1.0, rho0=1.0, p0=1.0e-5, r_cells=2.0):
+def sedov(n, gamma=5.0 / 3.0, E=1.0, rho0=1.0, p0=1.0e-5, r_cells=2.0, window=None):
     """Sedov-Taylor blast on [0,1]^3: E spread uniformly over the cells whose
-    centre lies within r_cells cell widths of the box centre."""
+    centre lies within r_cells cell widths of the box centre.  With
+    window = w, only the central w^3 cells of the n^3 box are returned (the
+    rest of the box is the uniform background state)."""
     x, dx = cell_centres(n)
+    if window is not None:
+        a = n // 2 - window // 2
+        x = x[a:a + window]
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
     inside = r < r_cells * dx
-    U = conserved(np.full((n, n, n), rho0), 0.0, 0.0, 0.0, p0, gamma)
+    U = conserved(np.full(X.shape, rho0), 0.0, 0.0, 0.0, p0, gamma)
     U[4][inside] += E / (inside.sum() * dx ** 3)
     return U
 
