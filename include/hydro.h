@@ -62,7 +62,7 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge
 #define HYDRO_OK 0
 #define HYDRO_EINVAL (-1)       /* bad argument (null pointer, size, enum)        */
 #define HYDRO_EGHOST (-2)       /* ghost width below what the scheme needs        */
-#define HYDRO_EUNSUPPORTED (-3) /* valid but not built (e.g. N other than 8, 16)  */
+#define HYDRO_EUNSUPPORTED (-3) /* valid but not built (e.g. N other than 16)     */
 #define HYDRO_ECUDA (-4)        /* a CUDA call failed (see hydro_last_cuda_error) */
 #define HYDRO_EWORKSPACE (-5)   /* workspace missing or smaller than required     */
 #define HYDRO_ETOOBIG (-6)      /* input larger than a fixed-size entry point takes */
@@ -128,7 +128,8 @@ int hydro_max_block_threads(const hydro_params* p, int N);
  *   flux       device [G][6][5][N][N] or NULL: fluxes through the six faces
  *              of each group (step (5), for the coarse-fine correction).
  *   dev_status device unsigned[G] or NULL: HYDRO_ST_* bits of each group.
- *   G >= 0 (0 is a no-op), N in {8, 16}, ghost >= hydro_required_ghost.
+ *   G >= 0 (0 is a no-op), N = 16 (the only group size built; others
+ *   return HYDRO_EUNSUPPORTED), ghost >= hydro_required_ghost.
  */
 int hydro_advance(const hydro_params* p, const void* U_in, void* U_out, void* flux, int G, int N, int ghost,
                   unsigned* dev_status, void* stream);
@@ -147,8 +148,12 @@ int hydro_gather_uniform(const void* field, int X, int Y, int Z, int bc, const i
 /*
  * hydro_advance_uniform — gather fused into the step for a uniform box tiled
  * by N^3 groups (group index (gz*GY + gy)*GX + gx): every CTA reads its
- * group's halo straight from field_in with the boundary condition bc and
- * writes its interior to field_out (double buffering; no aliasing).
+ * groups' halos straight from field_in with the boundary condition bc and
+ * writes their interiors to field_out (double buffering; no aliasing).  Each
+ * CTA takes a contiguous run of groups in column order (z fastest) and
+ * streams through the z-consecutive ones without restarting; the bytes of
+ * field_out, flux and dev_status are those of the same groups advanced one by
+ * one (gather + hydro_advance), whatever the launch shape.
  *   field_in, field_out  device [5][Z][Y][X]; X, Y, Z multiples of N.
  *   flux, dev_status     as hydro_advance, indexed by that group order.
  */

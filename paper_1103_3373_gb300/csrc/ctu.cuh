@@ -18,7 +18,9 @@
 //          on the group boundary are stored at once (step (5));
 //       A: load of the next input plane (primitives).
 // Every corrected state feeds exactly one face, so correcting inside the face
-// item recomputes nothing.  The stages are flat loops of the CTA's threads
+// item recomputes nothing.  In a uniform field the CTA streams through a
+// chain of K groups stacked along z (planes 0..KN-1) without restarting, so
+// the planes between two groups are traced and solved once.  The stages are flat loops of the CTA's threads
 // over the plane's work items (Sec. 3.1's index flattening).
 //
 // Index ranges (interior coordinates, cells 0..N-1): traced states on the
@@ -106,7 +108,8 @@ template <class T> __device__ __forceinline__ T correct(T u, T h1, T a1p, T a1m,
 }
 
 template <class T, class S, bool MIXED, int RS, int REC, int LIM, int N>
-__device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
+__device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K,
+                                               unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = CtuLayout<N, S_>;
   constexpr int L = Lay::L, LL = Lay::LL, LW = Lay::LW;
@@ -116,13 +119,13 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
   const int nthr = blockDim.x;
   const int tid = threadIdx.x;
   const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
-  unsigned st = 0;
+  const int NP = K * N;
 
   // prologue: the planes the first tracing needs
   for (int p = -1 - S_; p <= -1 + S_; ++p) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, p, 1 + S_, Wr);
   __syncthreads();
 
-  constexpr int T_ITERS = N + 4;
+  const int T_ITERS = NP + 4;
   for (int t = 0; t < T_ITERS; ++t) {
     const int q = t - 1;  // plane traced and given stage-1 fluxes
     const int r = q - 1;  // plane given stage-2 fluxes
@@ -131,7 +134,7 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
     {
       // the update's reads of U^n are issued first and consumed after the
       // tracing, so their latency hides behind it
-      const int nf = (u >= 0 && u < N) ? N * N : 0;
+      const int nf = (u >= 0 && u < NP) ? N * N : 0;
       T Un0[5];
       const bool pre_f = tid < nf;
       if (pre_f) {
@@ -139,7 +142,7 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
 #pragma unroll
         for (int v = 0; v < 5; ++v) Un0[v] = (T)C.load_raw(v, i, j, u);
       }
-      if (q <= N) {
+      if (q <= NP) {
         for (int k = tid; k < 3 * LL; k += nthr) {
           int d = k / LL;
           int rem = k - d * LL;
@@ -164,13 +167,13 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           dF[1][v] = R.F2y(u, v, j + 1, i) - R.F2y(u, v, j, i);
           dF[2][v] = R.F2z(u + 1, v, j, i) - R.F2z(u, v, j, i);
         }
-        st |= update_cell_from<T, S, MIXED, N>(C, i, j, u, Uc, dF, o.gas);
+        mark_status<N>(sts, K, u, 0, 0, update_cell_from<T, S, MIXED, N>(C, i, j, u, Uc, dF, o.gas));
       }
     }
     __syncthreads();
 
     // ---- S2: C, stage-1 fluxes (x/y faces of plane q, z faces below it) --
-    if (q <= N) {
+    if (q <= NP) {
       constexpr int NX = L * (N + 1);
       const int nz = q >= 0 ? LL : 0;
       const int cnt = 2 * NX + nz;
@@ -207,19 +210,23 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
         T UL[5], UR[5], F[5];
         load_local(pl, LL, lc, UL);
         load_local(pr, LL, lc, UR);
-        st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+        const unsigned s = riemann_local<T, MIXED, RS>(UL, UR, o, F);
         store_local(pf, fs, lc, F);
+        // a group's own stage-1 fluxes: x/y faces of its planes [-1, N], z
+        // faces below its planes [0, N]
+        mark_status<N>(sts, K, q, d == 2 ? 0 : -1, 1, s);
       }
     }
     __syncthreads();
 
     // ---- S3: E, corrected stage-2 fluxes of plane r; A, next input plane --
     {
-      const int nx = (r >= 0 && r < N) ? N * (N + 1) : 0;
-      const int nz = (r >= 0 && r <= N) ? N * N : 0;
+      const int nx = (r >= 0 && r < NP) ? N * (N + 1) : 0;
+      const int nz = (r >= 0 && r <= NP) ? N * N : 0;
+      const int rk = r >= 0 ? r / N : 0;  // chain group of plane r
       const int ne = 2 * nx + nz;
       const int pa = q + 1 + S_;  // plane the next tracing needs last
-      const int na = (pa <= N + S_) ? LW * LW : 0;
+      const int na = (pa <= NP + S_) ? LW * LW : 0;
       // the next plane's global loads are issued first and converted after
       // the Riemann work, so their latency hides behind it
       // the load items go to the threads with the fewest face items: thread t
@@ -260,7 +267,7 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           fs = N * (N + 1);
           if (f == 0 || f == N) {
             bface = f == 0 ? 0 : 1;
-            ba = r;
+            ba = r - rk * N;
             bb = j;
           }
         } else if (idx < 2 * nx) {
@@ -284,7 +291,7 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           fs = (N + 1) * N;
           if (f == 0 || f == N) {
             bface = f == 0 ? 2 : 3;
-            ba = r;
+            ba = r - rk * N;
             bb = i;
           }
         } else {
@@ -306,8 +313,8 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           b2m = &F1.y(r, 0, jj - 1, ii);
           pf = &R.F2z(r, 0, j, i);
           fs = N * N;
-          if (r == 0 || r == N) {
-            bface = r == 0 ? 4 : 5;
+          if (r == rk * N) {
+            bface = 4;  // -z face of group rk and +z face of group rk-1
             ba = j;
             bb = i;
           }
@@ -324,11 +331,19 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           UL[k] = correct(sl[v * LL], g1, a1p[v * s1], a1m[v * s1], g2, a2p[v * s2], a2m[v * s2]);
           UR[k] = correct(sr[v * LL], g1, b1p[v * s1], b1m[v * s1], g2, b2p[v * s2], b2m[v * s2]);
         }
-        st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+        const unsigned s = riemann_local<T, MIXED, RS>(UL, UR, o, F);
         store_local(pf, fs, lc, F);
+        mark_status<N>(sts, K, r, 0, d == 2 ? 1 : 0, s);
         if (bface >= 0) {
 #pragma unroll
-          for (int k = 0; k < 5; ++k) C.store_flux(bface, gv[k], ba, bb, F[k]);
+          for (int k = 0; k < 5; ++k) {
+            if (bface < 4) {
+              C.store_flux(rk, bface, gv[k], ba, bb, F[k]);
+            } else {
+              if (rk < K) C.store_flux(rk, 4, gv[k], ba, bb, F[k]);
+              if (rk > 0) C.store_flux(rk - 1, 5, gv[k], ba, bb, F[k]);
+            }
+          }
         }
       }
       for (int k = atid; atid >= 0 && k < na; k += naw) {
@@ -347,15 +362,14 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
     }
     __syncthreads();
   }
-  if (st) atomicOr(&st_sh, st);
 }
 
 template <class T, class S, bool MIXED, int RS, int REC, int N>
-__device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
+__device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   if (o.limiter == LIM_MINMOD && o.theta == T(1))
-    ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD1, N>(C, o, ring, st_sh);
+    ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD1, N>(C, o, ring, K, sts);
   else
-    ctu_group_impl<T, S, MIXED, RS, REC, -1, N>(C, o, ring, st_sh);
+    ctu_group_impl<T, S, MIXED, RS, REC, -1, N>(C, o, ring, K, sts);
 }
 
 }  // namespace hyd

@@ -17,9 +17,14 @@ struct SegDesc {
   const double* dt_dev; // optional device dt
   double dt;
   double dx[3];
-  int G, mode, bc, X, Y, Z, GX, GY;
+  int G, mode, bc, X, Y, Z, GX, GY, GZ;
   int first;            // flat index of this entry's first group
 };
+
+// Longest run of z-consecutive groups of a uniform field that one CTA streams
+// through without restarting (the ring buffers carry over from one group to
+// the next, so the ghost planes between them are traced once).
+constexpr int CHAIN_MAX = 32;
 
 struct WorkTable {
   int nseg;
@@ -34,11 +39,20 @@ struct KConst {
   long long ring_elems;  // per-CTA scratch elements (global-memory rings)
 };
 
-// Addressing of one group's input / output and its step constants.
+// Addressing of one group's input / output and its step constants.  In a
+// uniform field (mode 1) the context may cover a chain of groups stacked
+// along z; plane z of the chain then belongs to group z / N of the chain.
+//
+// Work order: mode 0 entries in list order; mode 1 entries column by column
+// (z fastest), so that consecutive work items are z-neighbours.  The user's
+// group index (flux and status arrays) is x-fastest:
+//   gu = gx + GX (gy + GY gz).
 template <class T, class S, int N> struct GroupCtx {
   const S* in;
   S* out;
-  S* flux;
+  S* flux;            // boundary fluxes of the chain's first group
+  long long fstride;  // elements between the flux arrays of chain groups
+  int gu, ustride;    // user index of the first group; step between chain groups
   int mode, bc, g, M;
   long long Mpl;  // M*M
   int X, Y, Z, ox, oy, oz;
@@ -56,11 +70,12 @@ template <class T, class S, int N> struct GroupCtx {
       dtdx[d] = (T)sc[d];
       hdtdx[d] = (T)sc[3 + d];
     }
-    flux = sg.flux ? (S*)sg.flux + (long long)gi * 30 * N * N : nullptr;
     if (mode == 0) {
       in = (const S*)sg.in + (long long)gi * 5 * Mpl * M;
       out = (S*)sg.out + (long long)gi * 5 * N * N * N;
       bc = 0;
+      gu = gi;
+      ustride = 1;
     } else {
       in = (const S*)sg.in;
       out = (S*)sg.out;
@@ -69,14 +84,21 @@ template <class T, class S, int N> struct GroupCtx {
       Y = sg.Y;
       Z = sg.Z;
       XYZ = (long long)X * Y * Z;
-      int gx = gi % sg.GX;
-      int gy = (gi / sg.GX) % sg.GY;
-      int gz = gi / (sg.GX * sg.GY);
+      int gz = gi % sg.GZ;
+      int col = gi / sg.GZ;
+      int gx = col % sg.GX;
+      int gy = col / sg.GX;
       ox = gx * N;
       oy = gy * N;
       oz = gz * N;
+      gu = gx + sg.GX * (gy + sg.GY * gz);
+      ustride = sg.GX * sg.GY;
     }
+    fstride = (long long)ustride * 30 * N * N;
+    flux = sg.flux ? (S*)sg.flux + (long long)gu * 30 * N * N : nullptr;
   }
+  // User index of group k of the chain.
+  __device__ __forceinline__ int user_index(int k) const { return gu + k * ustride; }
 
   // Box-edge index map for -n <= a < 2n (ghost width <= box size): periodic
   // wrap or outflow clamp.
@@ -118,9 +140,10 @@ template <class T, class S, int N> struct GroupCtx {
     else
       out[v * XYZ + ((long long)(oz + z) * Y + (oy + y)) * X + (ox + x)] = val;
   }
-  // Boundary flux of face f (0..5) at transverse indices (a, b).
-  __device__ __forceinline__ void store_flux(int f, int v, int a, int b, T val) const {
-    if (flux) flux[((f * 5 + v) * N + a) * N + b] = (S)val;
+  // Boundary flux of face f (0..5) of chain group k at transverse indices
+  // (a, b).
+  __device__ __forceinline__ void store_flux(int k, int f, int v, int a, int b, T val) const {
+    if (flux) flux[k * fstride + ((f * 5 + v) * N + a) * N + b] = (S)val;
   }
 };
 
@@ -131,6 +154,18 @@ __device__ __forceinline__ void group_consts(const SegDesc& sg, double* sc) {
     sc[d] = dt / sg.dx[d];
     sc[3 + d] = 0.5 * dt / sg.dx[d];
   }
+}
+
+// ORs the status bits s into every group k < K of a chain whose own
+// (unchained) computation covers plane p, i.e. kN + lo <= p <= kN + N-1 + hi
+// (the caller guarantees p >= lo).  A group's status thus holds the same bits
+// whether it is advanced alone or inside a chain.
+template <int N>
+__device__ __forceinline__ void mark_status(unsigned* sts, int K, int p, int lo, int hi, unsigned s) {
+  if (!s) return;
+  int k = (p - lo) / N;
+  if (k > K - 1) k = K - 1;
+  for (; k >= 0 && p <= k * N + N - 1 + hi; --k) atomicOr(&sts[k], s);
 }
 
 // Slot of plane p in a ring of R planes (p >= -8).

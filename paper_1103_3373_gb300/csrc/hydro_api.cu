@@ -254,6 +254,7 @@ int hydro_advance_uniform(const hydro_params* p, const void* field_in, void* fie
   s.Z = Z;
   s.GX = X / N;
   s.GY = Y / N;
+  s.GZ = Z / N;
   s.first = 0;
   return launch_table(p, wt, N, hydro_required_ghost(p->scheme, p->recon), stream);
 }
@@ -292,6 +293,7 @@ int hydro_advance_levels(const hydro_params* p, const hydro_level* levels, int n
       s.Z = lv.Z;
       s.GX = lv.X / N;
       s.GY = lv.Y / N;
+      s.GZ = lv.Z / N;
     }
     if (G > 0 && (!lv.U_in || !lv.U_out || lv.U_in == lv.U_out)) return HYDRO_EINVAL;
     s.in = lv.U_in;

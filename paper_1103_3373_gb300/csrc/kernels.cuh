@@ -1,7 +1,9 @@
-// Persistent patch-group kernel: each CTA walks the flat list of groups of
-// all work-table entries (levels / boxes / one batch) with stride gridDim.x
-// and runs the selected scheme on each (Sec. 3.1: one thread block per patch
-// group; here the blocks are persistent, one per SM).
+// Persistent patch-group kernel: each CTA takes a contiguous share of the
+// flat list of groups of all work-table entries (levels / boxes / one batch;
+// the shares differ by at most one group) and runs the selected scheme on it
+// (Sec. 3.1: one thread block per patch group; here the blocks are
+// persistent, one per SM).  In a uniform field consecutive work items are
+// z-neighbours, and a CTA streams through each run of them as one chain.
 #pragma once
 #include "ctu.cuh"
 #include "mhm.cuh"
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
   using S = typename Tr::S;
   constexpr bool MIXED = Tr::P::MIXED;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ unsigned st_sh;
+  __shared__ unsigned sts[CHAIN_MAX];  // status of the groups of the current chain
   __shared__ double sc[6];
   T* ring;
   if constexpr (Tr::SMEM)
@@ -50,27 +52,38 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
   o.theta = (T)kc.theta;
   o.limiter = kc.limiter;
   o.fallback = kc.fallback;
-  if (threadIdx.x == 0) st_sh = 0;
-  for (int w = blockIdx.x; w < wt.total; w += gridDim.x) {
+  if (threadIdx.x < CHAIN_MAX) sts[threadIdx.x] = 0;
+  const int b = blockIdx.x;
+  const int per = wt.total / gridDim.x, extra = wt.total % gridDim.x;
+  int w = b * per + (b < extra ? b : extra);
+  const int wend = w + per + (b < extra ? 1 : 0);
+  while (w < wend) {
     int s = 0;
     while (s + 1 < wt.nseg && w >= wt.seg[s + 1].first) ++s;
     const SegDesc& sg = wt.seg[s];
     const int gi = w - sg.first;
+    int K = 1;
+    if (sg.mode == 1) {
+      const int left = sg.GZ - gi % sg.GZ;  // groups left in this column
+      K = wend - w < left ? wend - w : left;
+      K = K < CHAIN_MAX ? K : CHAIN_MAX;
+    }
     if (threadIdx.x == 0) group_consts(sg, sc);
     __syncthreads();
     GroupCtx<T, S, N> C;
     C.init(sg, gi, kc, sc);
     if constexpr (SCH == CTU)
-      ctu_group<T, S, MIXED, RS, REC, N>(C, o, ring, st_sh);
+      ctu_group<T, S, MIXED, RS, REC, N>(C, o, ring, K, sts);
     else if constexpr (SCH == MHM)
-      mhm_group<T, S, MIXED, RS, REC, N>(C, o, ring, st_sh);
+      mhm_group<T, S, MIXED, RS, REC, N>(C, o, ring, K, sts);
     else
-      vl_group<T, S, MIXED, RS, REC, N>(C, o, ring, st_sh);
+      vl_group<T, S, MIXED, RS, REC, N>(C, o, ring, K, sts);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      if (sg.status) sg.status[gi] = st_sh;
-      st_sh = 0;
+    if (threadIdx.x < K) {
+      if (sg.status) sg.status[C.user_index(threadIdx.x)] = sts[threadIdx.x];
+      sts[threadIdx.x] = 0;
     }
+    w += K;
   }
 }
 

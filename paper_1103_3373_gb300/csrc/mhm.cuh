@@ -6,6 +6,9 @@
 // of a cell are evaluated before moving to the next cell, so the fluxes stay
 // in registers.  Then 3 Riemann solves per cell and the update.
 //
+// In a uniform field the CTA streams through a chain of K groups stacked
+// along z (planes 0..KN-1) without restarting.
+//
 // Iteration t:  F  update of plane pB-2 (completed by the previous iteration)
 //               A  load plane pA = t-1-S as primitives
 //               B  reconstruct + predict the 6 face states of the cells
@@ -59,26 +62,26 @@ __device__ __forceinline__ void mhm_faces(const WRing& Wr, int p, int jj, int ii
 }
 
 template <class T, class S, bool MIXED, int RS, int REC, int N>
-__device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
+__device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = MhmLayout<N, S_>;
   constexpr int L = Lay::L, LL = L * L, LW = Lay::LW;
   PlaneRing<T, LW, 2 * S_ + 1> Wr{ring};
   FaceRings<T, N, 1, 2> R{ring + Lay::OFF_FR};
-  unsigned st = 0;
   const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
+  const int NP = K * N;
 
-  constexpr int T_ITERS = N + 3 + 2 * S_;
+  const int T_ITERS = NP + 3 + 2 * S_;
   for (int t = 0; t < T_ITERS; ++t) {
     const int pA = t - 1 - S_;
     const int pB = pA - S_;
     const int pF = pB - 2;
-    if (pF >= 0 && pF < N) st |= stage_update<T, S, MIXED, N>(C, o, R, pF);
-    if (pA <= N + S_) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, pA, 1 + S_, Wr);
+    if (pF >= 0 && pF < NP) stage_update<T, S, MIXED, N>(C, o, R, pF, K, sts);
+    if (pA <= NP + S_) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, pA, 1 + S_, Wr);
     __syncthreads();
 
     // B: reconstruction + half-step prediction of the cells of plane pB
-    if (pB >= -1 && pB <= N) {
+    if (pB >= -1 && pB <= NP) {
       for (int idx = threadIdx.x; idx < LL; idx += blockDim.x) {
         int jj = idx / L, ii = idx - jj * L;
         T Uf[3][2][5], Ff[3][2][5];
@@ -101,10 +104,9 @@ __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
     __syncthreads();
 
     // C: 3 Riemann solves per cell (x/y faces of plane pB, z faces below it)
-    if (pB >= 0 && pB <= N) st |= stage_flux2<T, S, MIXED, RS, N>(C, o, R, pB);
+    if (pB >= 0 && pB <= NP) stage_flux2<T, S, MIXED, RS, N>(C, o, R, pB, K, sts);
     __syncthreads();
   }
-  if (st) atomicOr(&st_sh, st);
 }
 
 }  // namespace hyd

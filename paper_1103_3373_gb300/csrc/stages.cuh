@@ -45,15 +45,19 @@ template <class T, int N, int DXY, int DZ> struct FaceRings {
   }
 };
 
-// Final Riemann solves of plane p: x and y faces of the interior cells of
-// plane p (if 0 <= p < N) and the z faces between planes p-1 and p (if
-// 0 <= p <= N).  Fluxes on the group boundary are stored at once (step (5)).
+// Final Riemann solves of chain plane p (0 <= p <= NP, NP = K N): x and y
+// faces of the interior cells of plane p (if p < NP) and the z faces between
+// planes p-1 and p.  Fluxes on a group boundary are stored at once (step
+// (5)); a z face between two groups of a chain is the +z face of the lower
+// and the -z face of the upper one.
 template <class T, class S, bool MIXED, int RS, int N, class FR>
-__device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p) {
+__device__ __forceinline__ void stage_flux2(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+                                            unsigned* sts) {
   constexpr int LL = FR::LL;
-  unsigned st = 0;
-  const int nx = (p < N) ? N * (N + 1) : 0;
+  const int NP = K * N;
+  const int nx = (p < NP) ? N * (N + 1) : 0;
   const int cnt = 2 * nx + N * N;
+  const int pk = p / N;  // chain group of plane p (K for the top face)
   for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
     const T *pl, *pr;
     T* pf;
@@ -67,7 +71,7 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
       fs = N * (N + 1);
       if (f == 0 || f == N) {
         bface = f == 0 ? 0 : 1;
-        ba = p;
+        ba = p - pk * N;
         bb = j;
       }
     } else if (idx < 2 * nx) {
@@ -80,7 +84,7 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
       fs = (N + 1) * N;
       if (f == 0 || f == N) {
         bface = f == 0 ? 2 : 3;
-        ba = p;
+        ba = p - pk * N;
         bb = i;
       }
     } else {
@@ -91,8 +95,8 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
       pr = &R.Zs(p, 0, 0, j + 1, i + 1);
       pf = &R.F2z(p, 0, j, i);
       fs = N * N;
-      if (p == 0 || p == N) {
-        bface = p == 0 ? 4 : 5;
+      if (p == pk * N) {
+        bface = 4;
         ba = j;
         bb = i;
       }
@@ -101,21 +105,28 @@ __device__ __forceinline__ unsigned stage_flux2(const GroupCtx<T, S, N>& C, cons
     T UL[5], UR[5], F[5];
     load_local(pl, LL, lc, UL);
     load_local(pr, LL, lc, UR);
-    st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+    const unsigned s = riemann_local<T, MIXED, RS>(UL, UR, o, F);
     store_local(pf, fs, lc, F);
+    mark_status<N>(sts, K, p, 0, d == 2 ? 1 : 0, s);
     if (bface >= 0) {
       const int gv[5] = {0, lc.c1, lc.c2, lc.c3, 4};
 #pragma unroll
-      for (int k = 0; k < 5; ++k) C.store_flux(bface, gv[k], ba, bb, F[k]);
+      for (int k = 0; k < 5; ++k) {
+        if (bface < 4) {
+          C.store_flux(pk, bface, gv[k], ba, bb, F[k]);
+        } else {
+          if (pk < K) C.store_flux(pk, 4, gv[k], ba, bb, F[k]);
+          if (pk > 0) C.store_flux(pk - 1, 5, gv[k], ba, bb, F[k]);
+        }
+      }
     }
   }
-  return st;
 }
 
-// Conservative update of plane p from the final fluxes (step (4)).
+// Conservative update of chain plane p from the final fluxes (step (4)).
 template <class T, class S, bool MIXED, int N, class FR>
-__device__ __forceinline__ unsigned stage_update(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p) {
-  unsigned st = 0;
+__device__ __forceinline__ void stage_update(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+                                             unsigned* sts) {
   for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
     int j = idx / N, i = idx - j * N;
     T dF[3][5];
@@ -125,9 +136,8 @@ __device__ __forceinline__ unsigned stage_update(const GroupCtx<T, S, N>& C, con
       dF[1][v] = R.F2y(p, v, j + 1, i) - R.F2y(p, v, j, i);
       dF[2][v] = R.F2z(p + 1, v, j, i) - R.F2z(p, v, j, i);
     }
-    st |= update_cell<T, S, MIXED, N>(C, i, j, p, dF, o.gas);
+    mark_status<N>(sts, K, p, 0, 0, update_cell<T, S, MIXED, N>(C, i, j, p, dF, o.gas));
   }
-  return st;
 }
 
 // Ring of LW x LW input planes; the plane's lateral index ii maps to the

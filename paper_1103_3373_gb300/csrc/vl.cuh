@@ -13,7 +13,9 @@
 //               D  reconstruct plane pD = pC-S of the half-step state
 //               E  final fluxes: x/y faces of plane pD, z faces below it
 // The half-step state covers the cells [-1-S, N+S]^2 of each plane, the
-// first-order fluxes the faces of those cells.
+// first-order fluxes the faces of those cells.  In a uniform field the CTA
+// streams through a chain of K groups stacked along z (planes 0..KN-1)
+// without restarting.
 #pragma once
 #include "stages.cuh"
 
@@ -52,7 +54,7 @@ template <class T, int N, int S> struct VlF1 {
 };
 
 template <class T, class S, bool MIXED, int RS, int REC, int N>
-__device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned& st_sh) {
+__device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = VlLayout<N, S_>;
   constexpr int L = Lay::L, LH = Lay::LH, LU = Lay::LU;
@@ -60,23 +62,23 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
   PlaneRing<T, LH, 2 * S_ + 1> Wh{ring + Lay::OFF_W};
   FaceRings<T, N, 1, 2> R{ring + Lay::OFF_FR};
   VlF1<T, N, S_> F1{ring + Lay::OFF_F1};
-  unsigned st = 0;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
+  const int NP = K * N;
 
-  constexpr int T_ITERS = N + 5 + 2 * S_;
+  const int T_ITERS = NP + 5 + 2 * S_;
   for (int t = 0; t < T_ITERS; ++t) {
     const int pA = t - 2 - S_;
     const int pC = pA - 1;
     const int pD = pC - S_;
     const int pF = pD - 2;
-    if (pF >= 0 && pF < N) st |= stage_update<T, S, MIXED, N>(C, o, R, pF);
-    if (pA <= N + 1 + S_) stage_load<false, T, S, MIXED, N, LU, 2>(C, o, pA, 2 + S_, Ur);
+    if (pF >= 0 && pF < NP) stage_update<T, S, MIXED, N>(C, o, R, pF, K, sts);
+    if (pA <= NP + 1 + S_) stage_load<false, T, S, MIXED, N, LU, 2>(C, o, pA, 2 + S_, Ur);
     __syncthreads();
 
     // B: first-order fluxes on the cell-centred data
-    if (pA <= N + 1 + S_) {
-      const bool xy = pA >= -1 - S_ && pA <= N + S_;
+    if (pA <= NP + 1 + S_) {
+      const bool xy = pA >= -1 - S_ && pA <= NP + S_;
       const int nx = xy ? LH * (LH + 1) : 0;
       const int nz = pA >= -1 - S_ ? LH * LH : 0;
       const int cnt = 2 * nx + nz;
@@ -113,14 +115,17 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
         T UL[5], UR[5], F[5];
         load_local(pl, PLU, lc, UL);
         load_local(pr, PLU, lc, UR);
-        st |= riemann_local<T, MIXED, RS>(UL, UR, o, F);
+        const unsigned s = riemann_local<T, MIXED, RS>(UL, UR, o, F);
         store_local(pf, fs, lc, F);
+        // a group's own first-order fluxes: x/y faces of its planes
+        // [-1-S, N+S], z faces below its planes [-1-S, N+1+S]
+        mark_status<N>(sts, K, pA, -1 - S_, d == 2 ? 2 + S_ : 1 + S_, s);
       }
     }
     __syncthreads();
 
     // C: unsplit half step of plane pC, U^{n+1/2} = U^n - S, then primitives
-    if (pC >= -1 - S_ && pC <= N + S_) {
+    if (pC >= -1 - S_ && pC <= NP + S_) {
       for (int idx = tid; idx < LH * LH; idx += nthr) {
         int jj = idx / LH, ii = idx - jj * LH;
         T Uh[5], W[5];
@@ -139,8 +144,8 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
     __syncthreads();
 
     // D: reconstruction of the half-step state on plane pD (no tracing)
-    if (pD >= -1 && pD <= N) {
-      const bool xy = pD >= 0 && pD < N;
+    if (pD >= -1 && pD <= NP) {
+      const bool xy = pD >= 0 && pD < NP;
       const int nx = xy ? L * N : 0;
       const int cnt = 2 * nx + N * N;
       for (int idx = tid; idx < cnt; idx += nthr) {
@@ -190,10 +195,9 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
     __syncthreads();
 
     // E: 3 Riemann solves per cell (x/y faces of plane pD, z faces below it)
-    if (pD >= 0 && pD <= N) st |= stage_flux2<T, S, MIXED, RS, N>(C, o, R, pD);
+    if (pD >= 0 && pD <= NP) stage_flux2<T, S, MIXED, RS, N>(C, o, R, pD, K, sts);
     __syncthreads();
   }
-  if (st) atomicOr(&st_sh, st);
 }
 
 }  // namespace hyd

@@ -80,6 +80,63 @@ def test_fused_uniform_equals_gather_then_advance(torch_dev, prec, scheme, recon
     np.testing.assert_array_equal(st2.cpu().numpy(), st.cpu().numpy())
 
 
+@pytest.mark.parametrize("prec,bc", [(H.FP64, 0), (H.FP32, 1), (H.FP32_MIXED, 0)])
+@pytest.mark.parametrize("scheme,recon,rs", [(O.CTU, O.PPM, O.ROE), (O.VL, O.PLM, O.ROE), (O.MHM, O.PPM, O.ROE)])
+def test_chained_columns_equal_single_groups(torch_dev, prec, bc, scheme, recon, rs):
+    """In a uniform field a CTA streams through runs of z-consecutive groups
+    (chains of at most 32) without restarting.  Field, boundary fluxes and the
+    status of every group equal those of the same groups advanced one by one
+    (gather + hydro_advance), whatever the grid (chains cut at other places)
+    and for columns longer than the longest chain.  A double rarefaction
+    along z centred on a group boundary (and one along x) makes Roe's
+    linearisation fail near the boundaries, so the fallback bit is set in
+    some groups and must land in the same groups."""
+    torch, dev = torch_dev
+    N = 16
+    X, Y, Z = 32, 16, 576  # 2 columns of 36 groups
+    g = O.required_ghost(scheme, recon)
+    z = (np.arange(Z) + 0.5) / Z
+    x = (np.arange(X) + 0.5) / X
+    y = (np.arange(Y) + 0.5) / Y
+    zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * (xx + 2 * yy)) * np.cos(6 * np.pi * zz)
+    vz = np.where(zz < 288.0 / Z, -2.0, 2.0) + 0.1 * np.sin(2 * np.pi * yy)
+    vx = np.where(xx < 0.5, -1.5, 1.5) * (np.abs(zz - 0.25) < 0.05)
+    vy = 0.2 * np.cos(2 * np.pi * xx)
+    U = quantise(W.conserved(rho, vx, vy, vz, 0.4 + 0.1 * rho, 1.4), prec)
+    dx = (1.0 / X, 1.0 / Y, 1.0 / Z)
+    dt = 0.2 / Z
+    _, ph = params_pair(scheme, recon, rs, prec, dt, dx, fallback=O.HLLE, pres_floor=1e-10, dens_floor=1e-10)
+    with_workspace(ph, dev)
+    dtp = tdtype(prec)
+    ft = torch.tensor(U, dtype=dtp, device=dev)
+    orig = torch.tensor(W.group_origins(X, Y, Z, N), dtype=torch.int32, device=dev)
+    G = orig.shape[0]
+    M = N + 2 * g
+    Ug = torch.empty((G, 5, M, M, M), dtype=dtp, device=dev)
+    H.hydro_gather_uniform(ft, orig, Ug, N=N, ghost=g, bc=bc, precision=prec)
+    Uo = torch.empty((G, 5, N, N, N), dtype=dtp, device=dev)
+    fl = torch.empty((G, 6, 5, N, N), dtype=dtp, device=dev)
+    st = torch.empty(G, dtype=torch.int32, device=dev)
+    H.hydro_advance(ph, Ug, Uo, fl, st)
+    torch.cuda.synchronize()
+    ref = W.scatter_groups(Uo.double().cpu().numpy(), X, Y, Z)
+    ref_fl, ref_st = fl.cpu().numpy(), st.cpu().numpy()
+    fb = (ref_st & H.ST_ROE_FALLBACK) != 0
+    assert fb.any() and not fb.all()
+    for grid in (1, 5, 7, 0):
+        ph.grid_ctas = grid
+        with_workspace(ph, dev)
+        out = torch.full_like(ft, float("nan"))
+        fl2 = torch.full_like(fl, float("nan"))
+        st2 = torch.full_like(st, -1)
+        H.hydro_advance_uniform(ph, ft, out, bc=bc, flux=fl2, status=st2)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.double().cpu().numpy(), ref)
+        np.testing.assert_array_equal(fl2.cpu().numpy(), ref_fl)
+        np.testing.assert_array_equal(st2.cpu().numpy(), ref_st)
+
+
 @pytest.mark.parametrize("prec", [H.FP64, H.FP32])
 def test_levels_batch_equals_separate_launches(torch_dev, prec):
     """Uneven per-level group lists with per-level dx and dt in one persistent
