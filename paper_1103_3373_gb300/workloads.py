@@ -237,3 +237,78 @@ def amr_levels(counts=(4096, 2500, 1500, 800), n0=128, seed=5, N=16, g=3, mach=1
         levels.append({"U": Ul, "dx": prev["dx"] / 2.0, "score": sl,
                        "flagged_fraction": float(np.mean(sl > threshold))})
     return levels
+
+
+def smooth_field(x, y, z, seed=7, mach=1.0, gamma=1.4, modes=6, kmax=3):
+    """Smooth periodic state at points (x, y, z) of the unit box: density and
+    pressure exp/affine in a few random Fourier modes of integer wavevector
+    (|k_i| <= kmax, seeded), three velocity components from further modes,
+    scaled so the peak |v| is about `mach` sound speeds.  Resolution-free, so
+    every AMR level samples the same field at its own cell centres."""
+    rng = np.random.default_rng(seed)
+
+    def series(amp):
+        k = rng.integers(-kmax, kmax + 1, size=(modes, 3))
+        k[np.all(k == 0, axis=1)] = (1, 0, 0)
+        ph = rng.uniform(0.0, 2.0 * np.pi, modes)
+        a = rng.uniform(0.5, 1.0, modes) * amp / modes
+        s = np.zeros(np.broadcast(x, y, z).shape)
+        for m in range(modes):
+            s = s + a[m] * np.sin(2.0 * np.pi * (k[m, 0] * x + k[m, 1] * y + k[m, 2] * z) + ph[m])
+        return s
+
+    rho = np.exp(series(0.6))
+    p = 1.0 + series(0.4)
+    c = np.sqrt(gamma)
+    v = [mach * c * series(1.0) for _ in range(3)]
+    return conserved(rho, v[0], v[1], v[2], p, gamma)
+
+
+def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0, gamma=1.4, N=16, full=None):
+    """Static AMR hierarchy on the periodic unit box, as a list of levels
+    {U [G][5][N][N][N], origin [G][3] (x, y, z corner in the level's cells),
+    box (X, Y, Z), dx (3 floats)}.
+
+    Level 0 tiles the n0^3 box.  Level l+1 refines, as octets (the 8 groups
+    of twice the resolution covering one level-l group), every level-l group
+    whose centre lies within radii[l] of `center` (periodic distance) and
+    whose 26 neighbour groups all exist at level l (proper nesting); with
+    full = l, level l+1 refines every group of level l instead.  The data of
+    every level are smooth_field sampled at that level's cell centres, so
+    coarse and fine data are independent samples (not averages) of one field.
+    Group order: level 0 x-fastest; level l+1 octet by octet in parent order,
+    children (dz, dy, dx) lexicographic."""
+    levels = []
+    origin = group_origins(n0, n0, n0, N)
+    for l in range(len(radii) + 1):
+        n = n0 * 2 ** l
+        if l > 0:
+            prev = levels[-1]
+            pn = n // 2
+            slots = {tuple(o // N) for o in prev["origin"]}
+            gp = pn // N
+            kids = []
+            for o in prev["origin"]:
+                s = o // N
+                cen = (o + N / 2) / pn
+                dvec = np.abs(cen - np.asarray(center))
+                dvec = np.minimum(dvec, 1.0 - dvec)
+                near = np.sqrt((dvec ** 2).sum()) <= radii[l - 1] if full != l - 1 else True
+                nbrs = all(((s[0] + i) % gp, (s[1] + j) % gp, (s[2] + k) % gp) in slots
+                           for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1))
+                if near and nbrs:
+                    for dz in range(2):
+                        for dy in range(2):
+                            for dx_ in range(2):
+                                kids.append((2 * o[0] + dx_ * N, 2 * o[1] + dy * N, 2 * o[2] + dz * N))
+            if not kids:
+                break
+            origin = np.asarray(kids, dtype=np.int32).reshape(-1, 3)
+        r = (np.arange(N) + 0.5) / n
+        U = np.empty((len(origin), 5, N, N, N))
+        for k, (x0, y0, z0) in enumerate(origin):
+            zz, yy, xx = np.meshgrid(z0 / n + r, y0 / n + r, x0 / n + r, indexing="ij")
+            U[k] = smooth_field(xx, yy, zz, seed=seed, mach=mach, gamma=gamma)
+        levels.append({"U": U, "origin": np.asarray(origin, dtype=np.int32), "box": (n, n, n),
+                       "dx": (1.0 / n,) * 3})
+    return levels
