@@ -37,7 +37,8 @@ class _OrcParams(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("recon", ctypes.c_int), ("limiter", ctypes.c_int),
                 ("riemann", ctypes.c_int), ("fallback", ctypes.c_int), ("theta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("dens_floor", ctypes.c_double),
-                ("pres_floor", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double * 3)]
+                ("pres_floor", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double * 3),
+                ("characteristic", ctypes.c_int)]
 
 
 @dataclass
@@ -53,10 +54,11 @@ class Params:
     pres_floor: float = 0.0
     dt: float = 0.0
     dx: tuple = field(default_factory=lambda: (1.0, 1.0, 1.0))
+    characteristic: int = 0  # 1: reconstruct characteristic variables (Sec. 2)
 
     def c(self):
         p = _OrcParams()
-        for k in ("scheme", "recon", "limiter", "riemann", "fallback"):
+        for k in ("scheme", "recon", "limiter", "riemann", "fallback", "characteristic"):
             setattr(p, k, int(getattr(self, k)))
         for k in ("theta", "gamma", "dens_floor", "pres_floor", "dt"):
             setattr(p, k, float(getattr(self, k)))
@@ -84,6 +86,7 @@ def lib():
         L.orc_limiter.restype = ctypes.c_double
         L.orc_limiter.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.orc_recon1d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, _dp, _dp]
+        L.orc_recon_line.argtypes = [ctypes.POINTER(_OrcParams), ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
         L.orc_trace.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, ctypes.c_double, _dp, _dp]
         L.orc_riemann.restype = ctypes.c_uint
         L.orc_riemann.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -163,6 +166,18 @@ def cfl_dt(U, dx, cfl, gamma=1.4, dens_floor=0.0, pres_floor=0.0):
 
 def limiter(kind, dL, dR, theta=1.0):
     return lib().orc_limiter(kind, theta, dL, dR)
+
+
+def recon_line(params: Params, d, W):
+    """Face values of a line of primitive states W [5][n] (global frame) laid
+    along direction d, as the schemes reconstruct them (primitive or
+    characteristic form per params).  Returns (WL, WR, slope) [5][n] for the
+    cells S..n-1-S (NaN elsewhere)."""
+    W = _f64(W)
+    n = W.shape[1]
+    WL, WR, sl = (np.full((5, n), np.nan) for _ in range(3))
+    lib().orc_recon_line(ctypes.byref(params.c()), int(d), _ptr(W), n, _ptr(WL), _ptr(WR), _ptr(sl))
+    return WL, WR, sl
 
 
 def recon1d(recon, limiter_kind, w, theta=1.0):

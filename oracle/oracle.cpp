@@ -27,6 +27,7 @@ struct OrcParams {
   int scheme, recon, limiter, riemann, fallback;
   double theta, gamma, dens_floor, pres_floor, dt;
   double dx[3];
+  int characteristic;
 };
 
 static Params<double> to_params(const OrcParams* p) {
@@ -42,6 +43,7 @@ static Params<double> to_params(const OrcParams* p) {
   P.gas.pres_floor = p->pres_floor;
   P.dt = p->dt;
   for (int d = 0; d < 3; ++d) P.dx[d] = p->dx[d];
+  P.characteristic = p->characteristic;
   return P;
 }
 
@@ -137,6 +139,29 @@ double orc_limiter(int limiter, double theta, double dL, double dR) {
 }
 
 // 1D reconstruction of w[0..n): faces of cells s..n-1-s (s = stencil).
+// Face values (and PLM slopes) of the cells S..n-1-S of a line of n
+// primitive states W [5][n] (global frame) laid along direction d, as the
+// schemes reconstruct them (primitive or characteristic form per p); outputs
+// [5][n], untouched outside that range.
+void orc_recon_line(const OrcParams* p, int d, const double* W, int n, double* WL, double* WR, double* slope) {
+  Params<double> P = to_params(p);
+  Field5<double> F(n);
+  for (int v = 0; v < 5; ++v)
+    for (int i = 0; i < n; ++i) F(v, i) = W[v * n + i];
+  Box B(1, 0);
+  B.st[d] = 1;
+  const int S = recon_stencil(P.recon);
+  for (int i = S; i < n - S; ++i) {
+    double l[5], r[5], s[5] = {0, 0, 0, 0, 0};
+    recon_cell(P, B, F, i, d, l, r, s);
+    for (int v = 0; v < 5; ++v) {
+      WL[v * n + i] = l[v];
+      WR[v * n + i] = r[v];
+      slope[v * n + i] = s[v];
+    }
+  }
+}
+
 void orc_recon1d(int recon, int limiter, double theta, const double* w, int n, double* wL, double* wR) {
   int s = recon_stencil(recon);
   for (int i = s; i < n - s; ++i) {

@@ -38,6 +38,7 @@ template <class R> struct Params {
   Gas<R> gas;
   R dt;
   R dx[3];
+  int characteristic = 0;  // reconstruct characteristic (1) or primitive (0) variables
 };
 
 inline int recon_stencil(int recon) { return recon == REC_PPM ? 2 : 1; }
@@ -93,17 +94,61 @@ template <class R> struct Field5 {
 
 // Face values (global-frame primitives) of cell i along d from the primitive
 // field W.  For PLM also returns the limited slopes.
+//
+// Sec. 2 lets the reconstruction act on primitive or on characteristic
+// variables.  Characteristic form (P.characteristic), in the frame of d:
+// every stencil value W_j is projected on the left eigenvectors of the
+// primitive Jacobian at cell i, alpha_a(j) = l_a(W_i) . W_j; each of the 5
+// fields alpha_a goes through the same scalar PLM / PPM with the same
+// limiter; the face values (and PLM slope) come back as sum_a alpha_a r_a(W_i),
+// waves added in the order 1..5 starting from zero.
 template <class R>
 inline void recon_cell(const Params<R>& P, const Box& B, const Field5<R>& W, long i, int d, R WLf[5], R WRf[5],
                        R slope[5]) {
   long st = B.st[d];
-  for (int v = 0; v < 5; ++v) {
-    const R* w = &W.a[v * W.M3 + i];
-    if (P.recon == REC_PPM)
-      ppm_faces(w, st, P.limiter, P.theta, &WLf[v], &WRf[v]);
-    else
-      plm_faces(w, st, P.limiter, P.theta, &WLf[v], &WRf[v], &slope[v]);
+  if (!P.characteristic) {
+    for (int v = 0; v < 5; ++v) {
+      const R* w = &W.a[v * W.M3 + i];
+      if (P.recon == REC_PPM)
+        ppm_faces(w, st, P.limiter, P.theta, &WLf[v], &WRf[v]);
+      else
+        plm_faces(w, st, P.limiter, P.theta, &WLf[v], &WRf[v], &slope[v]);
+    }
+    return;
   }
+  Sec<R> sec(SEC_RECON);
+  const int S = recon_stencil(P.recon);
+  R wg[5], wl[5];
+  W.get(i, wg);
+  to_local(wg, wl, d);
+  Eigen<R> e;
+  eigen_prim(wl, P.gas, e);
+  R al[5][5];  // [wave][stencil offset + 2]
+  for (int j = -S; j <= S; ++j) {
+    W.get(i + j * st, wg);
+    to_local(wg, wl, d);
+    for (int a = 0; a < 5; ++a) al[a][j + 2] = left_proj(e, a, wl);
+  }
+  R aL[5], aR[5], ad[5];
+  for (int a = 0; a < 5; ++a) {
+    if (P.recon == REC_PPM) {
+      ppm_faces(&al[a][2], 1, P.limiter, P.theta, &aL[a], &aR[a]);
+      ad[a] = R(0.0);
+    } else {
+      plm_faces(&al[a][2], 1, P.limiter, P.theta, &aL[a], &aR[a], &ad[a]);
+    }
+  }
+  R fl[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+  R fr[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+  R sl[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+  for (int a = 0; a < 5; ++a) {
+    add_right(e, a, aL[a], fl);
+    add_right(e, a, aR[a], fr);
+    add_right(e, a, ad[a], sl);
+  }
+  to_global(fl, WLf, d);
+  to_global(fr, WRf, d);
+  to_global(sl, slope, d);
 }
 
 // Physical flux along d of a global-frame face state (W primitive, U its
