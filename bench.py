@@ -60,10 +60,15 @@ def measured_peaks():
         return {}
 
 
+# Sources the headline kernel (CTU, primitive reconstruction, FP32) is built
+# from; the stored DRAM-traffic figure is used only while they are unchanged.
+HEADLINE_SOURCES = ("phys.cuh", "group.cuh", "stages.cuh", "ctu.cuh", "kernels.cuh", "k_ctu_fp32.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1103_3373_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in HEADLINE_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -209,8 +214,48 @@ def amr_leg(H, RT, W, torch, dev, steps=20):
     return out
 
 
-def serving_leg(H, torch, dev, n_requests=300):
-    """Serving: the first n_requests of the seeded Poisson stream (200/s;
+def amr_hierarchy_leg(H, RT, W, torch, dev, replays=10):
+    """Device AMR hierarchy (ghost zones interpolated in space and time,
+    coarse-grid correction by the stored fluxes, restriction): a 256^3
+    periodic base of 4096 groups and refined levels of 2504 / 1504 / 800
+    groups (octets nearest the box centre; smooth seeded field), adaptive
+    time steps (level l takes 2^l steps of dt0 / 2^l).  FP32 CTU+PPM+Roe,
+    two hierarchy steps per CUDA-graph replay; cell-updates count every
+    level's substeps.  Also the device time per kind of launch of one eager
+    step."""
+    t = time.perf_counter()
+    levels = W.amr_hierarchy(256, counts=(2500, 1500, 800), seed=5)
+    gen_s = time.perf_counter() - t
+    p = make_params(H, H.FP32, (1.0, 1.0, 1.0))
+    hier = RT.AmrHierarchy(levels, p, device=dev)
+    dt0 = hier.compute_dt(CFL)
+    out = {"groups_per_level": [len(lv["origin"]) for lv in levels], "generate_s": gen_s, "dt0": dt0,
+           "cells_per_step": hier.cells_per_step, "launches_per_step": hier.launches_per_step()}
+    split = hier.step_timed(dt0)
+    hier.capture(dt0)
+    hier.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(replays):
+        hier.replay()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / (2 * replays)
+    out["fp32_graph"] = {"value": hier.cells_per_step / (ms / 1e3), "ms_per_step": ms, "steps": 2 * replays}
+    tot = sum(split.values())
+    out["eager_split_ms"] = {k: round(v, 3) for k, v in split.items()}
+    out["eager_split_share"] = {k: round(v / tot, 4) for k, v in split.items()}
+    out["errors"] = hier.errors()
+    out["state_finite"] = bool(all(torch.isfinite(u).all().item() for u in hier.cur))
+    out["unit"] = UNIT
+    del hier
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_leg(H, torch, dev, n_requests=2000):
+    """Serving: the n_requests of the seeded Poisson stream (200/s;
     boxes 32/64/128/256^3 with weights .4/.3/.2/.1; Mach 0.5-3; 5-50 steps;
     FP32 CTU+PPM+Roe), admitted by an HBM budget of half the free memory."""
     from paper_1103_3373_gb300 import serving as SV
@@ -417,10 +462,11 @@ def main():
                            "block_threads": tb["block_threads"] if tb else bx.p.block_threads}
             del bx
             torch.cuda.empty_cache()
-        for tag, sch, rec, rs in (("vl_plm_hllc_fp32", H.VL, H.PLM, H.RS_HLLC),
-                                  ("mhm_ppm_roe_fp32", H.MHM, H.PPM, H.RS_ROE)):
+        for tag, sch, rec, rs, ch in (("vl_plm_hllc_fp32", H.VL, H.PLM, H.RS_HLLC, 0),
+                                      ("mhm_ppm_roe_fp32", H.MHM, H.PPM, H.RS_ROE, 0),
+                                      ("ctu_ppm_roe_characteristic_fp32", H.CTU, H.PPM, H.RS_ROE, 1)):
             p = make_params(H, H.FP32, dx)
-            p.scheme, p.recon, p.riemann = sch, rec, rs
+            p.scheme, p.recon, p.riemann, p.characteristic = sch, rec, rs, ch
             bx = RT.UniformBox(U, p, cfl=CFL, device=dev, stream=stream)
             tb = bx.tune()
             bx.compute_dt()
@@ -430,6 +476,7 @@ def main():
             del bx
         torch.cuda.empty_cache()
         extra["amr_levels"] = amr_leg(H, RT, W, torch, dev)
+        extra["amr_hierarchy"] = amr_hierarchy_leg(H, RT, W, torch, dev)
         torch.cuda.empty_cache()
         extra["serving"] = serving_leg(H, torch, dev)
 

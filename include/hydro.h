@@ -95,6 +95,13 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge
  *   workspace    device scratch for the FP64 kernels (their stage buffers do
  *                not fit in shared memory); size from hydro_workspace_bytes.
  *                May be NULL when that size is 0.
+ *   characteristic  0: PLM / PPM act on the primitive variables; 1: on the
+ *                characteristic variables (Sec. 2: the reconstruction "can
+ *                be applied to either"): the stencil is projected on the left
+ *                eigenvectors of the primitive Jacobian at the cell along the
+ *                sweep, each wave is reconstructed with the same scalar PLM /
+ *                PPM and limiter, and the faces are projected back with the
+ *                right eigenvectors.  Same ghost widths.
  */
 typedef struct hydro_params {
   int scheme, recon, limiter, riemann, roe_fallback, precision;
@@ -105,6 +112,7 @@ typedef struct hydro_params {
   int block_threads, grid_ctas;
   void* workspace;
   size_t workspace_bytes;
+  int characteristic;
 } hydro_params;
 
 /* Ghost layers the scheme needs (Sec. 2): MHM and CTU 2 (PLM) / 3 (PPM);

@@ -34,8 +34,9 @@ def units():
 
 
 def deps():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "hydro.h"),
-                                                                 os.path.abspath(__file__)]
+    inc = os.path.join(ROOT, "include")
+    return ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] +
+            [os.path.join(inc, f) for f in os.listdir(inc)] + [os.path.abspath(__file__)])
 
 
 def needs_build():

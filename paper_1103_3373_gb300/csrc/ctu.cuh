@@ -66,12 +66,13 @@ template <class T, int N, int S> struct CtuF1 {
 };
 
 // Step (1) for one cell along direction d (known at run time; one inlined
-// copy serves all three): reconstruction of the primitive ring around
+// copy serves all three): reconstruction (of primitive or, with CH, of
+// characteristic variables) of the primitive ring around
 // (jj, ii) of plane p, characteristic tracing to t + dt/2.  The
 // rotation into the local frame is folded into the shared-memory addressing;
 // the traced states come back in the local frame (Ul, Ur conserved, normal
 // momentum first).
-template <int REC, int LIM, class T, class WRing>
+template <int REC, int LIM, bool CH, class T, class WRing>
 __device__ __forceinline__ void trace_cell_rt(const WRing& Wr, int p, int jj, int ii, int d, const LocalComps& lc,
                                               const Opts<T>& o, T dtdx, T Ul[5], T Ur[5]) {
   constexpr int S_ = REC == PPM ? 2 : 1;
@@ -88,7 +89,7 @@ __device__ __forceinline__ void trace_cell_rt(const WRing& Wr, int p, int jj, in
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) W0[v] = w[v][2];
-  recon5<REC, LIM>(w, o, WLf, WRf, dW);
+  recon5_local<REC, LIM, CH>(w, o, WLf, WRf, dW);
   T tl[5], tr[5];
   if (REC == PPM)
     trace_ppm(W0, WLf, WRf, dtdx, o.gas, tl, tr);
@@ -107,7 +108,7 @@ template <class T> __device__ __forceinline__ T correct(T u, T h1, T a1p, T a1m,
   return u;
 }
 
-template <class T, class S, bool MIXED, int RS, int REC, int LIM, int N>
+template <class T, class S, bool MIXED, int RS, int REC, int LIM, bool CH, int N>
 __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K,
                                                unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
@@ -149,7 +150,7 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
           int jj = rem / L, ii = rem - jj * L;
           T Ul[5], Ur[5];
           const LocalComps lc(d);
-          trace_cell_rt<REC, LIM>(Wr, q, jj, ii, d, lc, o, d == 0 ? C.dtdx[0] : (d == 1 ? C.dtdx[1] : C.dtdx[2]),
+          trace_cell_rt<REC, LIM, CH>(Wr, q, jj, ii, d, lc, o, d == 0 ? C.dtdx[0] : (d == 1 ? C.dtdx[1] : C.dtdx[2]),
                                   Ul, Ur);
           T* dl = d < 2 ? &R.XY(q, d, 0, 0, jj, ii) : &R.Zs(q, 0, 0, jj, ii);
           T* dr = d < 2 ? &R.XY(q, d, 1, 0, jj, ii) : &R.Zs(q, 1, 0, jj, ii);
@@ -364,12 +365,12 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
   }
 }
 
-template <class T, class S, bool MIXED, int RS, int REC, int N>
+template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N>
 __device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   if (o.limiter == LIM_MINMOD && o.theta == T(1))
-    ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD1, N>(C, o, ring, K, sts);
+    ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD1, CH, N>(C, o, ring, K, sts);
   else
-    ctu_group_impl<T, S, MIXED, RS, REC, -1, N>(C, o, ring, K, sts);
+    ctu_group_impl<T, S, MIXED, RS, REC, -1, CH, N>(C, o, ring, K, sts);
 }
 
 }  // namespace hyd

@@ -49,6 +49,16 @@ int cuda_fail(cudaError_t e) {
   return HYDRO_ECUDA;
 }
 
+}  // namespace
+
+// Shared with the other C-ABI translation units: records the CUDA error for
+// hydro_last_cuda_error and returns HYDRO_ECUDA.
+namespace hyd {
+int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+}  // namespace hyd
+
+namespace {
+
 void ensure_registered(State& s) {
   if (s.registered) return;
   memset(s.tab, 0, sizeof(s.tab));
@@ -61,6 +71,15 @@ void ensure_registered(State& s) {
   hyd_reg_ctu_fp64(s.tab);
   hyd_reg_ctu_fp32(s.tab);
   hyd_reg_ctu_mixed(s.tab);
+  hyd_reg_mhm_char_fp64(s.tab);
+  hyd_reg_mhm_char_fp32(s.tab);
+  hyd_reg_mhm_char_mixed(s.tab);
+  hyd_reg_vl_char_fp64(s.tab);
+  hyd_reg_vl_char_fp32(s.tab);
+  hyd_reg_vl_char_mixed(s.tab);
+  hyd_reg_ctu_char_fp64(s.tab);
+  hyd_reg_ctu_char_fp32(s.tab);
+  hyd_reg_ctu_char_mixed(s.tab);
   s.registered = true;
 }
 
@@ -85,6 +104,7 @@ int device_sms(State& s, int dev) {
 
 bool valid_enums(const hydro_params* p) {
   return p->scheme >= 0 && p->scheme <= 2 && p->recon >= 0 && p->recon <= 1 && p->limiter >= 0 && p->limiter <= 3 &&
+         (p->characteristic == 0 || p->characteristic == 1) &&
          p->riemann >= 0 && p->riemann <= 3 && p->precision >= 0 && p->precision <= 2 &&
          (p->riemann != HYDRO_RS_ROE ||
           (p->roe_fallback == HYDRO_RS_HLLE || p->roe_fallback == HYDRO_RS_HLLC || p->roe_fallback == HYDRO_RS_EXACT));
@@ -113,7 +133,7 @@ int resolve(const hydro_params* p, int N, long long total_groups, Launch& L) {
   if (rc) return rc;
   int nsm = device_sms(s, L.dev);
   if (nsm <= 0) return cuda_fail(cudaErrorInvalidDevice);
-  L.key = kernel_key(p->scheme, p->recon, p->riemann, p->precision);
+  L.key = kernel_key(p->scheme, p->recon, p->characteristic, p->riemann, p->precision);
   L.k = &s.tab[L.key];
   if (!L.k->fn) return HYDRO_EUNSUPPORTED;
   int maxt = L.k->max_threads;
@@ -190,7 +210,7 @@ int hydro_max_block_threads(const hydro_params* p, int N) {
   State& s = state();
   std::lock_guard<std::mutex> lk(s.mu);
   ensure_registered(s);
-  const KernelEntry& k = s.tab[kernel_key(p->scheme, p->recon, p->riemann, p->precision)];
+  const KernelEntry& k = s.tab[kernel_key(p->scheme, p->recon, p->characteristic, p->riemann, p->precision)];
   return k.fn ? k.max_threads : HYDRO_EUNSUPPORTED;
 }
 

@@ -29,7 +29,7 @@ template <int PR, int RS> struct MaxThreads {
   static constexpr int value = PR == P_FP64 ? 256 : (RS == RS_EXACT ? 384 : 512);
 };
 
-template <int SCH, int REC, int RS, int PR, int N>
+template <int SCH, int REC, int RS, int PR, int N, bool CH>
 __global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
     advance_kernel(const __grid_constant__ WorkTable wt, const KConst kc, void* ws) {
   using Tr = KTraits<SCH, REC, PR, N>;
@@ -73,11 +73,11 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
     GroupCtx<T, S, N> C;
     C.init(sg, gi, kc, sc);
     if constexpr (SCH == CTU)
-      ctu_group<T, S, MIXED, RS, REC, N>(C, o, ring, K, sts);
+      ctu_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
     else if constexpr (SCH == MHM)
-      mhm_group<T, S, MIXED, RS, REC, N>(C, o, ring, K, sts);
+      mhm_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
     else
-      vl_group<T, S, MIXED, RS, REC, N>(C, o, ring, K, sts);
+      vl_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
     __syncthreads();
     if (threadIdx.x < K) {
       if (sg.status) sg.status[C.user_index(threadIdx.x)] = sts[threadIdx.x];
@@ -96,33 +96,37 @@ struct KernelEntry {
   int smem;  // 1: rings in shared memory
 };
 
-constexpr int NKEY = 3 * 2 * 4 * 3;
-inline int kernel_key(int sch, int rec, int rs, int pr) { return ((sch * 2 + rec) * 4 + rs) * 3 + pr; }
+// (scheme, reconstruction, characteristic, solver, precision)
+constexpr int NKEY = 3 * 2 * 2 * 4 * 3;
+inline int kernel_key(int sch, int rec, int ch, int rs, int pr) {
+  return (((sch * 2 + rec) * 2 + ch) * 4 + rs) * 3 + pr;
+}
 
-template <int SCH, int REC, int RS, int PR, int N> inline void put_kernel(KernelEntry* tab) {
+template <int SCH, int REC, int RS, int PR, int N, bool CH> inline void put_kernel(KernelEntry* tab) {
   using Tr = KTraits<SCH, REC, PR, N>;
-  KernelEntry& e = tab[kernel_key(SCH, REC, RS, PR)];
-  e.fn = (const void*)&advance_kernel<SCH, REC, RS, PR, N>;
+  KernelEntry& e = tab[kernel_key(SCH, REC, CH ? 1 : 0, RS, PR)];
+  e.fn = (const void*)&advance_kernel<SCH, REC, RS, PR, N, CH>;
   e.ring_elems = Tr::RING;
   e.elem_bytes = (int)sizeof(typename Tr::T);
   e.max_threads = MaxThreads<PR, RS>::value;
   e.smem = Tr::SMEM ? 1 : 0;
 }
 
-template <int SCH, int PR, int N> inline void put_scheme(KernelEntry* tab) {
-  put_kernel<SCH, PLM, RS_EXACT, PR, N>(tab);
-  put_kernel<SCH, PLM, RS_HLLE, PR, N>(tab);
-  put_kernel<SCH, PLM, RS_HLLC, PR, N>(tab);
-  put_kernel<SCH, PLM, RS_ROE, PR, N>(tab);
-  put_kernel<SCH, PPM, RS_EXACT, PR, N>(tab);
-  put_kernel<SCH, PPM, RS_HLLE, PR, N>(tab);
-  put_kernel<SCH, PPM, RS_HLLC, PR, N>(tab);
-  put_kernel<SCH, PPM, RS_ROE, PR, N>(tab);
+template <int SCH, int PR, int N, bool CH> inline void put_scheme(KernelEntry* tab) {
+  put_kernel<SCH, PLM, RS_EXACT, PR, N, CH>(tab);
+  put_kernel<SCH, PLM, RS_HLLE, PR, N, CH>(tab);
+  put_kernel<SCH, PLM, RS_HLLC, PR, N, CH>(tab);
+  put_kernel<SCH, PLM, RS_ROE, PR, N, CH>(tab);
+  put_kernel<SCH, PPM, RS_EXACT, PR, N, CH>(tab);
+  put_kernel<SCH, PPM, RS_HLLE, PR, N, CH>(tab);
+  put_kernel<SCH, PPM, RS_HLLC, PR, N, CH>(tab);
+  put_kernel<SCH, PPM, RS_ROE, PR, N, CH>(tab);
 }
 
 }  // namespace hyd
 
-// Registration functions, one per (scheme, precision) translation unit.
+// Registration functions, one per (scheme, reconstructed variables,
+// precision) translation unit.
 #define HYD_DECLARE_REG(name) void name(hyd::KernelEntry* tab)
 HYD_DECLARE_REG(hyd_reg_mhm_fp64);
 HYD_DECLARE_REG(hyd_reg_mhm_fp32);
@@ -133,3 +137,12 @@ HYD_DECLARE_REG(hyd_reg_vl_mixed);
 HYD_DECLARE_REG(hyd_reg_ctu_fp64);
 HYD_DECLARE_REG(hyd_reg_ctu_fp32);
 HYD_DECLARE_REG(hyd_reg_ctu_mixed);
+HYD_DECLARE_REG(hyd_reg_mhm_char_fp64);
+HYD_DECLARE_REG(hyd_reg_mhm_char_fp32);
+HYD_DECLARE_REG(hyd_reg_mhm_char_mixed);
+HYD_DECLARE_REG(hyd_reg_vl_char_fp64);
+HYD_DECLARE_REG(hyd_reg_vl_char_fp32);
+HYD_DECLARE_REG(hyd_reg_vl_char_mixed);
+HYD_DECLARE_REG(hyd_reg_ctu_char_fp64);
+HYD_DECLARE_REG(hyd_reg_ctu_char_fp32);
+HYD_DECLARE_REG(hyd_reg_ctu_char_mixed);

@@ -9,11 +9,15 @@
 // In a uniform field the CTA streams through a chain of K groups stacked
 // along z (planes 0..KN-1) without restarting.
 //
-// Iteration t:  F  update of plane pB-2 (completed by the previous iteration)
-//               A  load plane pA = t-1-S as primitives
-//               B  reconstruct + predict the 6 face states of the cells
-//                  [-1,N]^2 of plane pB = pA-S
-//               C  final fluxes: x/y faces of plane pB, z faces below it
+// The planes -1-S..-1+S are loaded first; iteration t then runs two barrier
+// intervals for the plane pB = t-1:
+//   1  F  update of plane pB-2 (its fluxes are complete);
+//      B  reconstruct + predict the 6 face states of the cells [-1,N]^2 of
+//         plane pB;
+//   2  A  global reads of the input plane pA = pB+S+1 issued into registers,
+//      C  final fluxes: x/y faces of plane pB, z faces below it,
+//      A  then converted to primitives and stored in the ring (in the slot
+//         of plane pB-S, which B has finished with).
 #pragma once
 #include "stages.cuh"
 
@@ -37,9 +41,10 @@ template <int D, class T> __device__ __forceinline__ void pflux_global(const T W
   rot_out<D>(fl, F);
 }
 
-// Reconstruction along D of the cell (jj, ii) of plane p, its two face states
-// (conserved) and their physical fluxes along D.
-template <int D, int REC, class T, class WRing>
+// Reconstruction along D of the cell (jj, ii) of plane p (primitive
+// variables, or with CH characteristic ones in the frame of D), its two face
+// states (conserved) and their physical fluxes along D.
+template <int D, int REC, bool CH, class T, class WRing>
 __device__ __forceinline__ void mhm_faces(const WRing& Wr, int p, int jj, int ii, const Opts<T>& o, T Uf[2][5],
                                           T Ff[2][5]) {
   constexpr int S_ = REC == PPM ? 2 : 1;
@@ -53,7 +58,23 @@ __device__ __forceinline__ void mhm_faces(const WRing& Wr, int p, int jj, int ii
       else w[v][o2 + 2] = Wr(p + o2, v, jj + S_, ii + S_);
     }
   }
-  recon5<REC>(w, o, Wf[0], Wf[1], dW);
+  if constexpr (CH) {
+    T wl[5][5], fl[2][5];
+#pragma unroll
+    for (int o2 = 2 - S_; o2 <= 2 + S_; ++o2) {
+      T g[5], l[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[v] = w[v][o2];
+      rot_in<D>(g, l);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) wl[v][o2] = l[v];
+    }
+    recon5c<REC>(wl, o, fl[0], fl[1], dW);
+    rot_out<D>(fl[0], Wf[0]);
+    rot_out<D>(fl[1], Wf[1]);
+  } else {
+    recon5<REC>(w, o, Wf[0], Wf[1], dW);
+  }
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     cons(Wf[s], Uf[s], o.gas);
@@ -61,7 +82,7 @@ __device__ __forceinline__ void mhm_faces(const WRing& Wr, int p, int jj, int ii
   }
 }
 
-template <class T, class S, bool MIXED, int RS, int REC, int N>
+template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N>
 __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = MhmLayout<N, S_>;
@@ -70,24 +91,25 @@ __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
   FaceRings<T, N, 1, 2> R{ring + Lay::OFF_FR};
   const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
   const int NP = K * N;
+  const int tid = threadIdx.x, nthr = blockDim.x;
 
-  const int T_ITERS = NP + 3 + 2 * S_;
+  for (int p = -1 - S_; p <= -1 + S_; ++p) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, p, 1 + S_, Wr);
+  __syncthreads();
+
+  const int T_ITERS = NP + 3;
   for (int t = 0; t < T_ITERS; ++t) {
-    const int pA = t - 1 - S_;
-    const int pB = pA - S_;
+    const int pB = t - 1;
     const int pF = pB - 2;
+    const int pA = pB + S_ + 1;
+    // ---- 1: F (update of plane pF) and B (prediction of plane pB) ---------
     if (pF >= 0 && pF < NP) stage_update<T, S, MIXED, N>(C, o, R, pF, K, sts);
-    if (pA <= NP + S_) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, pA, 1 + S_, Wr);
-    __syncthreads();
-
-    // B: reconstruction + half-step prediction of the cells of plane pB
-    if (pB >= -1 && pB <= NP) {
-      for (int idx = threadIdx.x; idx < LL; idx += blockDim.x) {
+    if (pB <= NP) {
+      for (int idx = tid; idx < LL; idx += nthr) {
         int jj = idx / L, ii = idx - jj * L;
         T Uf[3][2][5], Ff[3][2][5];
-        mhm_faces<0, REC>(Wr, pB, jj, ii, o, Uf[0], Ff[0]);
-        mhm_faces<1, REC>(Wr, pB, jj, ii, o, Uf[1], Ff[1]);
-        mhm_faces<2, REC>(Wr, pB, jj, ii, o, Uf[2], Ff[2]);
+        mhm_faces<0, REC, CH>(Wr, pB, jj, ii, o, Uf[0], Ff[0]);
+        mhm_faces<1, REC, CH>(Wr, pB, jj, ii, o, Uf[1], Ff[1]);
+        mhm_faces<2, REC, CH>(Wr, pB, jj, ii, o, Uf[2], Ff[2]);
         // S = dt/(2dx) (Fx(R) - Fx(L)) + dt/(2dy) (...) + dt/(2dz) (...)
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -103,8 +125,36 @@ __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
     }
     __syncthreads();
 
-    // C: 3 Riemann solves per cell (x/y faces of plane pB, z faces below it)
-    if (pB >= 0 && pB <= NP) stage_flux2<T, S, MIXED, RS, N>(C, o, R, pB, K, sts);
+    // ---- 2: A (next input plane) around C (3 Riemann solves per cell) -----
+    {
+      const int nx = (pB >= 0 && pB < NP) ? N * (N + 1) : 0;
+      const int ne = (pB >= 0 && pB <= NP) ? 2 * nx + N * N : 0;
+      const int na = (pA <= NP + S_) ? LW * LW : 0;
+      // load items go to the threads with the fewest face items (thread t
+      // has one face item more than the others below ne % nthr)
+      const int aw0 = ne % nthr;
+      const int naw = nthr - aw0;
+      const int atid = tid - aw0;
+      T Ua0[5];
+      if (atid >= 0 && atid < na) {
+        int jj = atid / LW, ii = atid - jj * LW;
+        C.load5(ii - 1 - S_, jj - 1 - S_, pA, Ua0);
+      }
+      if (ne) stage_flux2<T, S, MIXED, RS, N>(C, o, R, pB, K, sts);
+      for (int k = atid; atid >= 0 && k < na; k += naw) {
+        int jj = k / LW, ii = k - jj * LW;
+        T U[5], W[5];
+        if (k == atid) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) U[v] = Ua0[v];
+        } else {
+          C.load5(ii - 1 - S_, jj - 1 - S_, pA, U);
+        }
+        prim<T, MIXED>(U, W, o.gas);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Wr(pA, v, jj, ii) = W[v];
+      }
+    }
     __syncthreads();
   }
 }

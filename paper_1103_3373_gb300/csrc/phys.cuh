@@ -671,6 +671,23 @@ struct LocalComps {
       : c1(1 + d), c2(d == 2 ? 1 : d + 2), c3(d == 0 ? 3 : d) {}
 };
 
+// Global <-> local frame of a run-time direction d, by selects (no dynamic
+// register indexing): local (n, t1, t2) = (x, y, z), (y, z, x), (z, x, y).
+template <class T> __device__ __forceinline__ void to_local_rt(int d, const T g[5], T l[5]) {
+  l[0] = g[0];
+  l[1] = d == 0 ? g[1] : (d == 1 ? g[2] : g[3]);
+  l[2] = d == 0 ? g[2] : (d == 1 ? g[3] : g[1]);
+  l[3] = d == 0 ? g[3] : (d == 1 ? g[1] : g[2]);
+  l[4] = g[4];
+}
+template <class T> __device__ __forceinline__ void to_global_rt(int d, const T l[5], T g[5]) {
+  g[0] = l[0];
+  g[1] = d == 0 ? l[1] : (d == 1 ? l[3] : l[2]);
+  g[2] = d == 0 ? l[2] : (d == 1 ? l[1] : l[3]);
+  g[3] = d == 0 ? l[3] : (d == 1 ? l[2] : l[1]);
+  g[4] = l[4];
+}
+
 // Load / store a 5-vector in the local frame of direction d from / to memory
 // holding it in the global frame with element stride s.
 template <class T>

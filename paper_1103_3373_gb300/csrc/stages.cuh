@@ -185,4 +185,61 @@ __device__ __forceinline__ void recon5(const T w[5][5], const Opts<T>& o, T WLf[
   }
 }
 
+// Face values of one cell from a LOCAL-frame primitive stencil, in
+// characteristic variables (Sec. 2: the reconstruction may act on primitive
+// or characteristic variables): every stencil value is projected on the
+// left eigenvectors at the cell centre, alpha_a(j) = l_a(W_0) . W_j, each
+// alpha_a goes through the scalar PLM / PPM with the limiter, and the faces
+// (and PLM slope) return as sum_a alpha_a r_a(W_0), waves added in the order
+// 1..5 starting from zero.  Outputs in the local frame.
+template <int REC, int LIM = -1, class T>
+__device__ __forceinline__ void recon5c(const T w[5][5], const Opts<T>& o, T WLf[5], T WRf[5], T dW[5]) {
+  constexpr int S_ = REC == PPM ? 2 : 1;
+  T W0[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) W0[v] = w[v][2];
+  Eig<T> e;
+  eig(W0, o.gas, e);
+  T al[5][5];
+#pragma unroll
+  for (int j = 2 - S_; j <= 2 + S_; ++j) {
+    T X[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) X[v] = w[v][j];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) al[a][j] = lproj(e, a, X);
+  }
+  T aL[5], aR[5], ad[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    if (REC == PPM) {
+      ppm<LIM>(al[a][0], al[a][1], al[a][2], al[a][3], al[a][4], o.limiter, o.theta, aL[a], aR[a]);
+      ad[a] = T(0);
+    } else {
+      plm<LIM>(al[a][1], al[a][2], al[a][3], o.limiter, o.theta, aL[a], aR[a], ad[a]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    WLf[v] = T(0);
+    WRf[v] = T(0);
+    dW[v] = T(0);
+  }
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    radd(e, a, aL[a], WLf);
+    radd(e, a, aR[a], WRf);
+    radd(e, a, ad[a], dW);
+  }
+}
+
+// Primitive or characteristic reconstruction of a local-frame stencil.
+template <int REC, int LIM, bool CH, class T>
+__device__ __forceinline__ void recon5_local(const T w[5][5], const Opts<T>& o, T WLf[5], T WRf[5], T dW[5]) {
+  if constexpr (CH)
+    recon5c<REC, LIM>(w, o, WLf, WRf, dW);
+  else
+    recon5<REC, LIM>(w, o, WLf, WRf, dW);
+}
+
 }  // namespace hyd

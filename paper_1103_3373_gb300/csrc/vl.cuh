@@ -53,7 +53,7 @@ template <class T, int N, int S> struct VlF1 {
   }
 };
 
-template <class T, class S, bool MIXED, int RS, int REC, int N>
+template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N>
 __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = VlLayout<N, S_>;
@@ -177,7 +177,24 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
             else w[v][o2 + 2] = Wh(pD + o2, v, jj + S_, ii + S_);
           }
         }
-        recon5<REC>(w, o, Wf[0], Wf[1], dW);
+        if constexpr (CH) {
+          // characteristic variables in the frame of d
+          T wl[5][5], fl[2][5];
+#pragma unroll
+          for (int o2 = 2 - S_; o2 <= 2 + S_; ++o2) {
+            T g[5], l[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) g[v] = w[v][o2];
+            to_local_rt(d, g, l);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) wl[v][o2] = l[v];
+          }
+          recon5c<REC>(wl, o, fl[0], fl[1], dW);
+          to_global_rt(d, fl[0], Wf[0]);
+          to_global_rt(d, fl[1], Wf[1]);
+        } else {
+          recon5<REC>(w, o, Wf[0], Wf[1], dW);
+        }
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           T U[5];

@@ -25,6 +25,7 @@ NOALLOC_MAX_CELLS = (NOALLOC_MAX_PARTIALS // 3) * NOALLOC_CELLS_PER_CTA
 ST_ROE_FALLBACK, ST_NEG_DENS, ST_NEG_PRES, ST_NAN, ST_EXACT_FAIL = 1, 2, 4, 8, 16
 ST_ERROR_MASK = ST_NEG_DENS | ST_NEG_PRES | ST_NAN | ST_EXACT_FAIL
 MAX_LEVELS = 32
+AMR_ENESTING, AMR_EDUPLICATE, AMR_EOCTET = 1, 2, 4  # include/hydro_amr.h dev_error bits
 
 SCHEMES = {"mhm": MHM, "vl": VL, "ctu": CTU}
 RECONS = {"plm": PLM, "ppm": PPM}
@@ -48,7 +49,8 @@ class _CParams(ctypes.Structure):
                 ("theta", ctypes.c_double), ("gamma", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dx", ctypes.c_double * 3), ("dens_floor", ctypes.c_double), ("pres_floor", ctypes.c_double),
                 ("dt_dev", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("characteristic", ctypes.c_int)]
 
 
 class _CLevel(ctypes.Structure):
@@ -56,6 +58,11 @@ class _CLevel(ctypes.Structure):
                 ("status", ctypes.c_void_p), ("dt_dev", ctypes.c_void_p), ("dt", ctypes.c_double),
                 ("dx", ctypes.c_double * 3), ("G", ctypes.c_int), ("mode", ctypes.c_int), ("bc", ctypes.c_int),
                 ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int)]
+
+
+class _CAmrLevel(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("origin", ctypes.c_void_p), ("map", ctypes.c_void_p),
+                ("G", ctypes.c_int), ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int)]
 
 
 @dataclass
@@ -77,11 +84,12 @@ class Params:
     block_threads: int = 0
     grid_ctas: int = 0
     workspace: object = None
+    characteristic: int = 0  # 1: PLM / PPM on characteristic variables (Sec. 2)
 
     def c(self):
         p = _CParams()
         for k in ("scheme", "recon", "limiter", "riemann", "roe_fallback", "precision", "block_threads",
-                  "grid_ctas"):
+                  "grid_ctas", "characteristic"):
             setattr(p, k, int(getattr(self, k)))
         for k in ("theta", "gamma", "dt", "dens_floor", "pres_floor"):
             setattr(p, k, float(getattr(self, k)))
@@ -120,6 +128,11 @@ def _lib():
         L.hydro_conserved_totals.argtypes = [vp, i, ll, ll, ll, i, vp, vp, ctypes.c_size_t, vp]
         L.hydro_cfl_dt_noalloc.argtypes = [vp, i, ll, ll, ll, i, d, d, d, ctypes.POINTER(ctypes.c_double), d, vp,
                                            vp, vp]
+        A = ctypes.POINTER(_CAmrLevel)
+        L.hydro_amr_map.argtypes = [vp, i, i, i, i, i, vp, vp, vp]
+        L.hydro_amr_prepare.argtypes = [A, A, vp, d, i, i, i, i, vp, vp, vp]
+        L.hydro_amr_reflux.argtypes = [A, vp, A, vp, vp, d, ctypes.POINTER(ctypes.c_double), i, i, i, vp, vp]
+        L.hydro_amr_restrict.argtypes = [A, A, i, i, vp, vp]
         L.hydro_strerror.argtypes = [i]
         L.hydro_strerror.restype = ctypes.c_char_p
         L.hydro_last_cuda_error.argtypes = []
@@ -295,3 +308,66 @@ def hydro_cfl_dt_noalloc(U, dx, cfl, dt_out, gamma=1.4, dens_floor=0.0, pres_flo
                                      dxa, float(cfl), _ptr(dt_out, "dt_out", "float64"),
                                      _ptr(smax_out, "smax_out", "float64"), _stream(stream))
     _check(rc, "hydro_cfl_dt_noalloc")
+
+
+# ---------------------------------------------------------------- AMR (include/hydro_amr.h)
+
+@dataclass
+class AmrLevel:
+    """One level of an AMR hierarchy: U [G][5][N][N][N] (storage dtype),
+    origin int32 [G][3] (x, y, z corner in the level's cells), map int32
+    [Z/N][Y/N][X/N] (hydro_amr_map), box (X, Y, Z) in the level's cells."""
+    U: object
+    origin: object
+    map: object
+    box: tuple
+
+    def c(self, precision):
+        X, Y, Z = (int(a) for a in self.box)
+        G = int(self.origin.shape[0])
+        return _CAmrLevel(_ptr(self.U, "U", _storage_dtype(precision)), _ptr(self.origin, "origin", "int32"),
+                          _ptr(self.map, "map", "int32"), G, X, Y, Z)
+
+
+def hydro_amr_map(origin, box, map_out, N=16, error=None, stream=None):
+    """Group map of a level: map_out int32 [Z/N][Y/N][X/N] <- group index or -1."""
+    X, Y, Z = (int(a) for a in box)
+    G = int(origin.shape[0])
+    rc = _lib().hydro_amr_map(_ptr(origin, "origin", "int32") if G else None, G, X, Y, Z, N,
+                              _ptr(map_out, "map", "int32"), _ptr(error, "error", "int32"), _stream(stream))
+    _check(rc, "hydro_amr_map")
+
+
+def hydro_amr_prepare(fine: AmrLevel, coarse, coarse_new, theta, U_out, bc=BC_PERIODIC, N=16, ghost=3,
+                      precision=FP32, error=None, stream=None):
+    """Halo-padded input [G][5][M][M][M] of every group of `fine` (copy from
+    the level, else interpolation from `coarse` at time theta)."""
+    dt = _storage_dtype(precision)
+    cf = fine.c(precision)
+    cc = coarse.c(precision) if coarse is not None else None
+    rc = _lib().hydro_amr_prepare(ctypes.byref(cf), ctypes.byref(cc) if cc is not None else None,
+                                  _ptr(coarse_new, "coarse_new", dt), float(theta), bc, N, ghost, precision,
+                                  _ptr(U_out, "U_out", dt), _ptr(error, "error", "int32"), _stream(stream))
+    _check(rc, "hydro_amr_prepare")
+
+
+def hydro_amr_reflux(coarse: AmrLevel, coarse_flux, fine: AmrLevel, fine_flux0, fine_flux1, dt, dx,
+                     bc=BC_PERIODIC, N=16, precision=FP32, error=None, stream=None):
+    """Coarse-grid correction of coarse.U (in place) by the fine fluxes of the
+    two substeps."""
+    st = _storage_dtype(precision)
+    cc, cf = coarse.c(precision), fine.c(precision)
+    dxa = (ctypes.c_double * 3)(*[float(a) for a in dx])
+    rc = _lib().hydro_amr_reflux(ctypes.byref(cc), _ptr(coarse_flux, "coarse_flux", st), ctypes.byref(cf),
+                                 _ptr(fine_flux0, "fine_flux0", st), _ptr(fine_flux1, "fine_flux1", st), float(dt),
+                                 dxa, bc, N, precision, _ptr(error, "error", "int32"), _stream(stream))
+    _check(rc, "hydro_amr_reflux")
+
+
+def hydro_amr_restrict(fine: AmrLevel, coarse: AmrLevel, N=16, precision=FP32, error=None, stream=None):
+    """Coarse cells covered by fine groups take the mean of their 8 fine cells
+    (coarse.U in place)."""
+    cf, cc = fine.c(precision), coarse.c(precision)
+    rc = _lib().hydro_amr_restrict(ctypes.byref(cf), ctypes.byref(cc), N, precision, _ptr(error, "error", "int32"),
+                                   _stream(stream))
+    _check(rc, "hydro_amr_restrict")

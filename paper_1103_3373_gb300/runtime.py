@@ -212,3 +212,176 @@ class LevelBatch:
 
     def replay(self):
         self.graph.replay()
+
+
+class _NoTimer:
+    def __enter__(self):
+        return None
+
+    def __exit__(self, *exc):
+        return False
+
+
+def _no_timer(kind):
+    return _NoTimer()
+
+
+class AmrHierarchy:
+    """A static AMR hierarchy resident on the GPU (level 0 covers the box,
+    level l+1 refines whole level-l groups as octets; dx_l = dx_0 / 2^l),
+    stepped with adaptive time steps dt_l = dt_0 / 2^l entirely by library
+    kernels (include/hydro_amr.h and hydro_advance), recursively per level:
+
+      prepare  ghost zones of every group of level l: copies from level l,
+               else interpolation from level l-1 in space and in time
+               (theta = 0 for the first substep, 1/2 for the second; Sec. 4.2)
+      advance  hydro_advance of the level's groups, boundary fluxes stored
+               (Sec. 2 steps (1)-(5))
+      finer    level l+1 twice with dt_l / 2
+      reflux   coarse cells next to level l+1 take its fluxes (Sec. 4.3)
+      restrict coarse cells under level l+1 take the mean of its cells
+
+    No host synchronisation inside step(), so a step can be captured into a
+    CUDA graph (capture()/replay()).  `levels` is a list of dicts {U
+    [G][5][N][N][N], origin [G][3], box, dx} (workloads.amr_hierarchy).
+    """
+
+    def __init__(self, levels, params: H.Params, bc=H.BC_PERIODIC, N=16, device="cuda:0", stream=None):
+        import dataclasses
+        torch = _torch()
+        self.torch = torch
+        self.dev = torch.device(device)
+        self.bc, self.N, self.stream = bc, N, stream
+        self.prec = params.precision
+        dt = torch.float64 if self.prec == H.FP64 else torch.float32
+        self.ghost = H.hydro_required_ghost(params.scheme, params.recon)
+        M = N + 2 * self.ghost
+        self.L = len(levels)
+        self.err = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        self.origin, self.map, self.box, self.cur, self.new, self.Ug, self.flux, self.status = ([] for _ in range(8))
+        self.params = []
+        for l, lv in enumerate(levels):
+            G = len(lv["origin"])
+            X, Y, Z = lv["box"]
+            self.box.append((X, Y, Z))
+            self.origin.append(torch.as_tensor(np.asarray(lv["origin"], dtype=np.int32)).to(self.dev).contiguous())
+            m = torch.empty((Z // N, Y // N, X // N), dtype=torch.int32, device=self.dev)
+            H.hydro_amr_map(self.origin[l], (X, Y, Z), m, N=N, error=self.err, stream=stream)
+            self.map.append(m)
+            self.cur.append(torch.as_tensor(lv["U"], dtype=dt).to(self.dev).contiguous())
+            self.new.append(torch.empty_like(self.cur[l]))
+            self.Ug.append(torch.empty((G, 5, M, M, M), dtype=dt, device=self.dev))
+            nsub = 1 if l == 0 else 2
+            self.flux.append([torch.empty((G, 6, 5, N, N), dtype=dt, device=self.dev) for _ in range(nsub)])
+            self.status.append(torch.zeros(G, dtype=torch.int32, device=self.dev))
+            p = dataclasses.replace(params)
+            p.dx = tuple(float(a) for a in lv["dx"])
+            p.dt_dev = None
+            self.params.append(p)
+        nws = H.hydro_workspace_bytes(self.params[0], N)
+        ws = torch.empty(nws, dtype=torch.uint8, device=self.dev) if nws else None
+        for p in self.params:
+            p.workspace = ws
+        self.cells_per_step = sum(len(lv["origin"]) * N ** 3 * 2 ** l for l, lv in enumerate(levels))
+        self.graph = None
+
+    def level(self, l, U):
+        return H.AmrLevel(U=U, origin=self.origin[l], map=self.map[l], box=self.box[l])
+
+    def _step(self, l, dt, s, st, tm):
+        coarse = self.level(l - 1, self.cur[l - 1]) if l > 0 else None
+        coarse_new = self.new[l - 1] if (l > 0 and s == 1) else None
+        with tm("prepare"):
+            H.hydro_amr_prepare(self.level(l, self.cur[l]), coarse, coarse_new, 0.5 * s, self.Ug[l], bc=self.bc,
+                                N=self.N, ghost=self.ghost, precision=self.prec, error=self.err, stream=st)
+        p = self.params[l]
+        p.dt = dt
+        with tm("advance"):
+            H.hydro_advance(p, self.Ug[l], self.new[l], self.flux[l][s], self.status[l], N=self.N,
+                            ghost=self.ghost, stream=st)
+        if l + 1 < self.L:
+            self._step(l + 1, 0.5 * dt, 0, st, tm)
+            self._step(l + 1, 0.5 * dt, 1, st, tm)
+            with tm("reflux"):
+                H.hydro_amr_reflux(self.level(l, self.new[l]), self.flux[l][s], self.level(l + 1, self.cur[l + 1]),
+                                   self.flux[l + 1][0], self.flux[l + 1][1], dt, p.dx, bc=self.bc, N=self.N,
+                                   precision=self.prec, error=self.err, stream=st)
+            with tm("restrict"):
+                H.hydro_amr_restrict(self.level(l + 1, self.cur[l + 1]), self.level(l, self.new[l]), N=self.N,
+                                     precision=self.prec, error=self.err, stream=st)
+        self.cur[l], self.new[l] = self.new[l], self.cur[l]
+
+    def step(self, dt0, stream=None):
+        """One step of the whole hierarchy with base time step dt0."""
+        self._step(0, float(dt0), 0, stream if stream is not None else self.stream, _no_timer)
+
+    def step_timed(self, dt0):
+        """step() on the current stream with CUDA events around every launch;
+        returns the device milliseconds per kind of launch (prepare, advance,
+        reflux, restrict)."""
+        torch = self.torch
+        marks = []
+
+        class _T:
+            def __init__(self, kind):
+                self.kind = kind
+
+            def __enter__(self):
+                self.a = torch.cuda.Event(enable_timing=True)
+                self.a.record()
+
+            def __exit__(self, *exc):
+                b = torch.cuda.Event(enable_timing=True)
+                b.record()
+                marks.append((self.kind, self.a, b))
+
+        self._step(0, float(dt0), 0, None, _T)
+        torch.cuda.synchronize()
+        out = {}
+        for kind, a, b in marks:
+            out[kind] = out.get(kind, 0.0) + a.elapsed_time(b)
+        return out
+
+    def launches_per_step(self):
+        """Kernels one step enqueues: prepare + advance per level step, reflux +
+        restrict per refined level step."""
+        n = 0
+        for l in range(self.L):
+            n += 2 ** l * (2 + (2 if l + 1 < self.L else 0))
+        return n
+
+    def compute_dt(self, cfl=0.4):
+        """min over levels of 2^l x the CFL dt of level l (host value; one
+        device reduction per level)."""
+        torch = self.torch
+        ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=self.dev)
+        dts = torch.zeros(self.L, dtype=torch.float64, device=self.dev)
+        p = self.params[0]
+        for l in range(self.L):
+            H.hydro_cfl_dt(self.cur[l], self.params[l].dx, cfl, dts[l:l + 1], ws, gamma=p.gamma,
+                           dens_floor=p.dens_floor, pres_floor=p.pres_floor, precision=self.prec,
+                           stream=self.stream)
+        scale = torch.tensor([2.0 ** l for l in range(self.L)], dtype=torch.float64, device=self.dev)
+        return float((dts * scale).min().item())
+
+    def errors(self):
+        return int(self.err.item())
+
+    def capture(self, dt0):
+        """Capture two steps of dt0 into a CUDA graph (a graph replays fixed
+        buffers; level 0 swaps its double buffer once per step, the finer
+        levels an even number of times, so two steps bring every level back
+        to the buffers it started from).  capture_graph's warm-up runs the
+        two steps once eagerly; replay() then advances two steps each."""
+        st = self.torch.cuda.current_stream
+
+        def two():
+            self.step(dt0, st())
+            self.step(dt0, st())
+
+        self.graph = capture_graph(two)
+        return self.graph
+
+    def replay(self):
+        """Two steps (see capture)."""
+        self.graph.replay()

@@ -76,17 +76,19 @@ def gaussian_field(n, seed, slope=-3.0):
     return f
 
 
-def lognormal(n, seed=1, sigma=0.5, mach=1.5, gamma=1.4, p0=1.0, vel_seeds=None):
-    """Periodic lognormal box: rho = exp(sigma d - sigma^2/2), p = p0, and three
-    independent k^-3 velocity components scaled so that sqrt(<|v|^2/c^2>) = mach."""
+def lognormal(n, seed=1, sigma=0.5, mach=1.5, gamma=1.4, p0=1.0, vel_seeds=None, p_index=0.0):
+    """Periodic lognormal box: rho = exp(sigma d - sigma^2/2), p = p0 rho^p_index
+    (uniform by default), and three independent k^-3 velocity components
+    scaled so that sqrt(<|v|^2/c^2>) = mach."""
     d = gaussian_field(n, seed)
     rho = np.exp(sigma * d - 0.5 * sigma * sigma)
+    p = p0 * rho ** p_index if p_index else p0
     vs = vel_seeds or (seed + 1, seed + 2, seed + 3)
     v = [gaussian_field(n, s) for s in vs]
-    c2 = gamma * p0 / rho
+    c2 = gamma * p / rho
     m2 = (v[0] ** 2 + v[1] ** 2 + v[2] ** 2) / c2
     scale = mach / np.sqrt(m2.mean())
-    return conserved(rho, scale * v[0], scale * v[1], scale * v[2], p0, gamma)
+    return conserved(rho, scale * v[0], scale * v[1], scale * v[2], p, gamma)
 
 
 def sedov(n, gamma=5.0 / 3.0, E=1.0, rho0=1.0, p0=1.0e-5, r_cells=2.0, window=None):
@@ -240,21 +242,27 @@ def amr_levels(counts=(4096, 2500, 1500, 800), n0=128, seed=5, N=16, g=3, mach=1
 
 
 def smooth_field(x, y, z, seed=7, mach=1.0, gamma=1.4, modes=6, kmax=3):
-    """Smooth periodic state at points (x, y, z) of the unit box: density and
-    pressure exp/affine in a few random Fourier modes of integer wavevector
-    (|k_i| <= kmax, seeded), three velocity components from further modes,
-    scaled so the peak |v| is about `mach` sound speeds.  Resolution-free, so
-    every AMR level samples the same field at its own cell centres."""
+    """Smooth periodic state [5][nz][ny][nx] on the tensor grid of the 1-D
+    coordinate arrays x, y, z (unit box): density and pressure exp/affine in
+    a few random Fourier modes of integer wavevector (|k_i| <= kmax, seeded),
+    three velocity components from further modes, scaled so the peak |v| is
+    about `mach` sound speeds.  Resolution-free, so every AMR level samples
+    the same field at its own cell centres.  Each mode sin(2 pi k.x + phi) is
+    evaluated as the imaginary part of a product of 1-D complex exponentials."""
     rng = np.random.default_rng(seed)
+    x, y, z = (np.asarray(a, dtype=np.float64) for a in (x, y, z))
 
     def series(amp):
         k = rng.integers(-kmax, kmax + 1, size=(modes, 3))
         k[np.all(k == 0, axis=1)] = (1, 0, 0)
         ph = rng.uniform(0.0, 2.0 * np.pi, modes)
         a = rng.uniform(0.5, 1.0, modes) * amp / modes
-        s = np.zeros(np.broadcast(x, y, z).shape)
+        s = np.zeros((z.size, y.size, x.size))
         for m in range(modes):
-            s = s + a[m] * np.sin(2.0 * np.pi * (k[m, 0] * x + k[m, 1] * y + k[m, 2] * z) + ph[m])
+            ex = np.exp(1j * (2.0 * np.pi * k[m, 0] * x + ph[m]))
+            ey = np.exp(2j * np.pi * k[m, 1] * y)
+            ez = np.exp(2j * np.pi * k[m, 2] * z)
+            s = s + a[m] * (ez[:, None, None] * (ey[None, :, None] * ex[None, None, :])).imag
         return s
 
     rho = np.exp(series(0.6))
@@ -264,7 +272,8 @@ def smooth_field(x, y, z, seed=7, mach=1.0, gamma=1.4, modes=6, kmax=3):
     return conserved(rho, v[0], v[1], v[2], p, gamma)
 
 
-def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0, gamma=1.4, N=16, full=None):
+def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0, gamma=1.4, N=16, full=None,
+                  counts=None):
     """Static AMR hierarchy on the periodic unit box, as a list of levels
     {U [G][5][N][N][N], origin [G][3] (x, y, z corner in the level's cells),
     box (X, Y, Z), dx (3 floats)}.
@@ -273,14 +282,17 @@ def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0,
     of twice the resolution covering one level-l group), every level-l group
     whose centre lies within radii[l] of `center` (periodic distance) and
     whose 26 neighbour groups all exist at level l (proper nesting); with
-    full = l, level l+1 refines every group of level l instead.  The data of
+    full = l, level l+1 refines every group of level l instead; with counts
+    (groups wanted per refined level), level l+1 refines the ceil(counts[l] /
+    8) eligible level-l groups nearest to `center` instead of using radii.  The data of
     every level are smooth_field sampled at that level's cell centres, so
     coarse and fine data are independent samples (not averages) of one field.
     Group order: level 0 x-fastest; level l+1 octet by octet in parent order,
     children (dz, dy, dx) lexicographic."""
     levels = []
     origin = group_origins(n0, n0, n0, N)
-    for l in range(len(radii) + 1):
+    nref = len(counts) if counts is not None else len(radii)
+    for l in range(nref + 1):
         n = n0 * 2 ** l
         if l > 0:
             prev = levels[-1]
@@ -288,15 +300,25 @@ def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0,
             slots = {tuple(o // N) for o in prev["origin"]}
             gp = pn // N
             kids = []
+            dist = []
+            eligible = []
             for o in prev["origin"]:
                 s = o // N
                 cen = (o + N / 2) / pn
                 dvec = np.abs(cen - np.asarray(center))
                 dvec = np.minimum(dvec, 1.0 - dvec)
-                near = np.sqrt((dvec ** 2).sum()) <= radii[l - 1] if full != l - 1 else True
-                nbrs = all(((s[0] + i) % gp, (s[1] + j) % gp, (s[2] + k) % gp) in slots
-                           for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1))
-                if near and nbrs:
+                dist.append(np.sqrt((dvec ** 2).sum()))
+                eligible.append(all(((s[0] + i) % gp, (s[1] + j) % gp, (s[2] + k) % gp) in slots
+                                    for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)))
+            dist = np.asarray(dist)
+            if counts is not None:
+                order = [i for i in np.argsort(dist, kind="stable") if eligible[i]]
+                pick = set(order[:int(np.ceil(counts[l - 1] / 8))])
+            else:
+                pick = {i for i in range(len(dist))
+                        if eligible[i] and (full == l - 1 or dist[i] <= radii[l - 1])}
+            for i, o in enumerate(prev["origin"]):
+                if i in pick:
                     for dz in range(2):
                         for dy in range(2):
                             for dx_ in range(2):
@@ -307,8 +329,7 @@ def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0,
         r = (np.arange(N) + 0.5) / n
         U = np.empty((len(origin), 5, N, N, N))
         for k, (x0, y0, z0) in enumerate(origin):
-            zz, yy, xx = np.meshgrid(z0 / n + r, y0 / n + r, x0 / n + r, indexing="ij")
-            U[k] = smooth_field(xx, yy, zz, seed=seed, mach=mach, gamma=gamma)
+            U[k] = smooth_field(x0 / n + r, y0 / n + r, z0 / n + r, seed=seed, mach=mach, gamma=gamma)
         levels.append({"U": U, "origin": np.asarray(origin, dtype=np.int32), "box": (n, n, n),
                        "dx": (1.0 / n,) * 3})
     return levels

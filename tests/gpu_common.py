@@ -43,11 +43,13 @@ def rel_l1(a, b, axis_var=1):
 
 
 def params_pair(scheme, recon, riemann, prec, dt, dx, limiter=O.MINMOD, theta=1.0, fallback=O.HLLE, gamma=1.4,
-                dens_floor=0.0, pres_floor=0.0):
+                dens_floor=0.0, pres_floor=0.0, characteristic=0):
     po = O.Params(scheme=scheme, recon=recon, riemann=riemann, limiter=limiter, theta=theta, fallback=fallback,
-                  gamma=gamma, dens_floor=dens_floor, pres_floor=pres_floor, dt=dt, dx=dx)
+                  gamma=gamma, dens_floor=dens_floor, pres_floor=pres_floor, dt=dt, dx=dx,
+                  characteristic=characteristic)
     ph = H.Params(scheme=scheme, recon=recon, riemann=riemann, limiter=limiter, theta=theta, roe_fallback=fallback,
-                  precision=prec, gamma=gamma, dens_floor=dens_floor, pres_floor=pres_floor, dt=dt, dx=dx)
+                  precision=prec, gamma=gamma, dens_floor=dens_floor, pres_floor=pres_floor, dt=dt, dx=dx,
+                  characteristic=characteristic)
     return po, ph
 
 
@@ -74,7 +76,7 @@ def gpu_advance(ph, Ug, N=16, device="cuda:0", want_flux=True):
             st.cpu().numpy().astype(np.uint32))
 
 
-def lognormal_groups(n=32, N=16, g=3, seed=1, mach=1.5, prec=H.FP64):
-    U = W.lognormal(n, seed=seed, mach=mach)
+def lognormal_groups(n=32, N=16, g=3, seed=1, mach=1.5, prec=H.FP64, p_index=0.0):
+    U = W.lognormal(n, seed=seed, mach=mach, p_index=p_index)
     Uq = quantise(U, prec)
     return Uq, O.gather(Uq, W.group_origins(n, n, n, N), N, g, bc=0)

@@ -1,5 +1,5 @@
 """The C-ABI library builds here (nvcc cross-compiles sm_103a without a GPU),
-loads, and exports every entry point include/hydro.h declares.  No compute
+loads, and exports every entry point the headers in include/ declare.  No compute
 call is made (there is no GPU in the CPU suite)."""
 import ctypes
 import os
@@ -12,15 +12,20 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared():
-    src = open(os.path.join(ROOT, "include", "hydro.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(hydro_[a-z_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(hydro_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared()
     for n in ("hydro_advance", "hydro_advance_uniform", "hydro_advance_levels", "hydro_gather_uniform",
-              "hydro_cfl_dt", "hydro_required_ghost", "hydro_strerror"):
+              "hydro_cfl_dt", "hydro_required_ghost", "hydro_strerror", "hydro_amr_map", "hydro_amr_prepare",
+              "hydro_amr_reflux", "hydro_amr_restrict"):
         assert n in names
 
 
@@ -47,3 +52,18 @@ def test_product_package_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_binding_marshals_its_structs():
+    """Host-side marshalling of the binding (no device call): parameter and
+    level structs build from Python values with the header's field order."""
+    from paper_1103_3373_gb300 import hydro as H
+    p = H.Params(scheme=H.CTU, recon=H.PPM, riemann=H.RS_ROE, precision=H.FP32, dt=0.1, dx=(0.5, 0.25, 0.125))
+    c = p.c()
+    assert (c.scheme, c.recon, c.riemann, c.precision) == (H.CTU, H.PPM, H.RS_ROE, H.FP32)
+    assert tuple(c.dx) == (0.5, 0.25, 0.125) and c.dt == 0.1
+    names = [f[0] for f in H._CParams._fields_]
+    assert names[:6] == ["scheme", "recon", "limiter", "riemann", "roe_fallback", "precision"]
+    a = H._CAmrLevel(1, 2, 3, 4, 5, 6, 7)
+    assert (a.G, a.X, a.Y, a.Z) == (4, 5, 6, 7)
+    assert [f[0] for f in H._CAmrLevel._fields_] == ["U", "origin", "map", "G", "X", "Y", "Z"]
