@@ -7,7 +7,7 @@ The product package never imports it and has no CPU fallback.
 Thin ctypes wrapper over ``liboracle.so`` (built from the C++ sources in this
 folder by ``oracle/build.py``).  All arrays are float64 numpy arrays, C order.
 Enumerations follow the paper's names (Sec. 2):
-  scheme  MHM=0, VL=1, CTU=2;  recon PLM=0, PPM=1;
+  scheme  MHM=0, VL=1, CTU=2 (unsplit), RTVD=3, WAF=4 (split);  recon PLM=0, PPM=1;
   limiter MINMOD=0 (generalized, theta), VANLEER=1, VANALBADA=2, HYBRID=3;
   riemann EXACT=0, HLLE=1, HLLC=2, ROE=3 (fallback: EXACT/HLLE/HLLC).
 """
@@ -19,7 +19,7 @@ import numpy as np
 
 from . import build as _build
 
-MHM, VL, CTU = 0, 1, 2
+MHM, VL, CTU, RTVD, WAF = 0, 1, 2, 3, 4
 PLM, PPM = 0, 1
 MINMOD, VANLEER, VANALBADA, HYBRID = 0, 1, 2, 3
 EXACT, HLLE, HLLC, ROE = 0, 1, 2, 3
@@ -38,7 +38,7 @@ class _OrcParams(ctypes.Structure):
                 ("riemann", ctypes.c_int), ("fallback", ctypes.c_int), ("theta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("dens_floor", ctypes.c_double),
                 ("pres_floor", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double * 3),
-                ("characteristic", ctypes.c_int)]
+                ("characteristic", ctypes.c_int), ("split_order", ctypes.c_int)]
 
 
 @dataclass
@@ -55,10 +55,11 @@ class Params:
     dt: float = 0.0
     dx: tuple = field(default_factory=lambda: (1.0, 1.0, 1.0))
     characteristic: int = 0  # 1: reconstruct characteristic variables (Sec. 2)
+    split_order: int = 0     # RTVD / WAF: sweeps x, y, z (0) or z, y, x (1)
 
     def c(self):
         p = _OrcParams()
-        for k in ("scheme", "recon", "limiter", "riemann", "fallback", "characteristic"):
+        for k in ("scheme", "recon", "limiter", "riemann", "fallback", "characteristic", "split_order"):
             setattr(p, k, int(getattr(self, k)))
         for k in ("theta", "gamma", "dens_floor", "pres_floor", "dt"):
             setattr(p, k, float(getattr(self, k)))

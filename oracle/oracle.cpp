@@ -28,6 +28,7 @@ struct OrcParams {
   double theta, gamma, dens_floor, pres_floor, dt;
   double dx[3];
   int characteristic;
+  int split_order;
 };
 
 static Params<double> to_params(const OrcParams* p) {
@@ -44,6 +45,7 @@ static Params<double> to_params(const OrcParams* p) {
   P.dt = p->dt;
   for (int d = 0; d < 3; ++d) P.dx[d] = p->dx[d];
   P.characteristic = p->characteristic;
+  P.split_order = p->split_order;
   return P;
 }
 

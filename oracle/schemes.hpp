@@ -23,13 +23,14 @@
 // [z][y][x] order with the normal one removed, fluxes time-centred (not
 // multiplied by dt), positive along +axis.
 #pragma once
+#include <array>
 #include <vector>
 #include "reconstruct.hpp"
 #include "riemann.hpp"
 
 namespace orc {
 
-enum Scheme { SCH_MHM = 0, SCH_VL = 1, SCH_CTU = 2 };
+enum Scheme { SCH_MHM = 0, SCH_VL = 1, SCH_CTU = 2, SCH_RTVD = 3, SCH_WAF = 4 };
 enum Recon { REC_PLM = 0, REC_PPM = 1 };
 
 template <class R> struct Params {
@@ -39,6 +40,7 @@ template <class R> struct Params {
   R dt;
   R dx[3];
   int characteristic = 0;  // reconstruct characteristic (1) or primitive (0) variables
+  int split_order = 0;     // split schemes: sweeps x, y, z (0) or z, y, x (1)
 };
 
 inline int recon_stencil(int recon) { return recon == REC_PPM ? 2 : 1; }
@@ -46,8 +48,12 @@ inline int recon_stencil(int recon) { return recon == REC_PPM ? 2 : 1; }
 // Ghost layers a scheme needs: face states are required for the cells -1..N
 // along the normal; CTU also needs the stage-1 fluxes of the cells -1..N in
 // the lateral directions, which the same width provides.  VL reconstructs its
-// half-step state, which itself needs one more layer.
+// half-step state, which itself needs one more layer.  The split schemes need
+// their 1D stencil: RTVD 3 (first-order half step, then limited fluxes of
+// the half-step state), WAF 2 (the limiter reads the neighbouring fans).
 inline int required_ghost(int scheme, int recon) {
+  if (scheme == SCH_RTVD) return 3;
+  if (scheme == SCH_WAF) return 2;
   int s = recon_stencil(recon);
   return scheme == SCH_VL ? s + 2 : s + 1;
 }
@@ -428,10 +434,238 @@ template <class R> void ctu_group(const Params<R>& P, const Box& B, const R* Uin
   update_and_store(P, B, Uin, F, out);
 }
 
+// ---------------------------------------------------------------------------
+// The directionally split schemes Sec. 3.2 measures beside the unsplit ones
+// (RTVD and WAF): three 1D sweeps per step, x, y, z (split_order 0) or z, y,
+// x (1; the caller alternates them, Strang), each with the full dt, on the
+// local-frame conserved states of the rows along the sweep.  Each sweep
+// updates the cells [0, N) along its direction in the rows the later sweeps
+// still read: the first sweep every row whose transverse coordinates lie in
+// [-g, N+g), the second [0, N) along the first sweep's direction and
+// [-g, N+g) along the last's, the last [0, N)^2.  The fluxes of each sweep's
+// update through the group faces are the boundary fluxes of step (5).
+// ---------------------------------------------------------------------------
+
+// RTVD (relaxing TVD, Jin & Xin 1995, in the flux-split form of Trac & Pen
+// 2003).  Per cell the freezing speed c = |u_n| + c_s and the flux F;
+// right- and left-moving parts FR = (c U + F)/2, FL = (c U - F)/2.
+template <class R> inline void rtvd_split(const R U[5], const Gas<R>& gas, R FR[5], R FL[5]) {
+  R W[5], F[5];
+  prim_from_cons(U, W, gas);
+  R c = fabs(W[1]) + sound_speed(W[0], W[4], gas);
+  phys_flux_local(W, U[4], F);
+  for (int v = 0; v < 5; ++v) {
+    FR[v] = R(0.5) * (c * U[v] + F[v]);
+    FL[v] = R(0.5) * (c * U[v] - F[v]);
+  }
+}
+
+// One RTVD row u[0..n) (local frame; updated in place on [lo, hi), which
+// needs lo >= 3 and hi <= n - 3):
+//   half step, first-order upwind:  F1_{j+1/2} = FR_j - FL_{j+1},
+//     Uh_j = U_j - (dt/2dx) (F1_{j+1/2} - F1_{j-1/2});
+//   full step, limited fluxes of Uh (psi = limited slope of the limiter):
+//     FR_{i+1/2} = FR_i + psi(FR_i - FR_{i-1}, FR_{i+1} - FR_i) / 2,
+//     FL_{i+1/2} = FL_{i+1} - psi(FL_{i+1} - FL_i, FL_{i+2} - FL_{i+1}) / 2,
+//     U_i <- U_i - (dt/dx) (F_{i+1/2} - F_{i-1/2}),  F = FR - FL.
+// Returns the fluxes through lo - 1/2 and hi - 1/2.
+template <class R>
+inline void rtvd_row(const Params<R>& P, std::vector<std::array<R, 5>>& u, int lo, int hi, R dtdx, R hdtdx,
+                     R Flo[5], R Fhi[5]) {
+  const int n = (int)u.size();
+  std::vector<std::array<R, 5>> FR(n), FL(n), F1(n), FRh(n), FLh(n), FT(n);
+  for (int j = lo - 3; j < hi + 3; ++j) rtvd_split(u[j].data(), P.gas, FR[j].data(), FL[j].data());
+  for (int j = lo - 3; j < hi + 2; ++j)
+    for (int v = 0; v < 5; ++v) F1[j][v] = FR[j][v] - FL[j + 1][v];
+  for (int j = lo - 2; j < hi + 2; ++j) {
+    R uh[5];
+    for (int v = 0; v < 5; ++v) uh[v] = u[j][v] - hdtdx * (F1[j][v] - F1[j - 1][v]);
+    rtvd_split(uh, P.gas, FRh[j].data(), FLh[j].data());
+  }
+  for (int i = lo - 1; i < hi; ++i)
+    for (int v = 0; v < 5; ++v) {
+      R fr = FRh[i][v] + R(0.5) * limited_slope(P.limiter, P.theta, FRh[i][v] - FRh[i - 1][v],
+                                                FRh[i + 1][v] - FRh[i][v]);
+      R fl = FLh[i + 1][v] - R(0.5) * limited_slope(P.limiter, P.theta, FLh[i + 1][v] - FLh[i][v],
+                                                    FLh[i + 2][v] - FLh[i + 1][v]);
+      FT[i][v] = fr - fl;
+    }
+  for (int i = lo; i < hi; ++i)
+    for (int v = 0; v < 5; ++v) u[i][v] = u[i][v] - dtdx * (FT[i][v] - FT[i - 1][v]);
+  for (int v = 0; v < 5; ++v) {
+    Flo[v] = FT[lo - 1][v];
+    Fhi[v] = FT[hi - 1][v];
+  }
+}
+
+// The HLLC wave fan of one face (Toro 2009 ch. 10, with the Einfeldt speeds
+// of hllc_flux): speeds S = (SL, S*, SR), the fluxes of the four states
+// U_L, U*L, U*R, U_R (F*K = FK + SK (U*K - UK)), and the density jumps across
+// the three waves.
+template <class R> struct Fan {
+  R S[3];
+  R F[4][5];
+  R drho[3];
+};
+
+template <class R> inline void hllc_fan(const Side<R>& L, const Side<R>& Rs, const Gas<R>& gas, Fan<R>& f) {
+  RoeAvg<R> A;
+  roe_average(L, Rs, gas, A);
+  R a = A.a2 > R(0.0) ? sqrt(A.a2) : R(0.0);
+  R SL = L.W[1] - L.c;
+  R t = A.u - a;
+  if (t < SL) SL = t;
+  R SR = Rs.W[1] + Rs.c;
+  t = A.u + a;
+  if (t > SR) SR = t;
+  R mL = L.W[0] * (SL - L.W[1]);
+  R mR = Rs.W[0] * (SR - Rs.W[1]);
+  R Ss = (Rs.W[4] - L.W[4] + mL * L.W[1] - mR * Rs.W[1]) / (mL - mR);
+  R fL = mL / (SL - Ss), fR = mR / (SR - Ss);
+  R UsL[5] = {fL, fL * Ss, fL * L.W[2], fL * L.W[3], fL * (L.E / L.W[0] + (Ss - L.W[1]) * (Ss + L.W[4] / mL))};
+  R UsR[5] = {fR, fR * Ss, fR * Rs.W[2], fR * Rs.W[3],
+              fR * (Rs.E / Rs.W[0] + (Ss - Rs.W[1]) * (Ss + Rs.W[4] / mR))};
+  f.S[0] = SL;
+  f.S[1] = Ss;
+  f.S[2] = SR;
+  for (int v = 0; v < 5; ++v) {
+    f.F[0][v] = L.F[v];
+    f.F[1][v] = L.F[v] + SL * (UsL[v] - L.U[v]);
+    f.F[2][v] = Rs.F[v] + SR * (UsR[v] - Rs.U[v]);
+    f.F[3][v] = Rs.F[v];
+  }
+  f.drho[0] = UsL[0] - L.W[0];
+  f.drho[1] = UsR[0] - UsL[0];
+  f.drho[2] = Rs.W[0] - UsR[0];
+}
+
+// One WAF row (Toro 2009 ch. 14, TVD version with the HLLC fan): with
+// c_k = (dt/dx) S_k,
+//   F_{i+1/2} = (F_1 + F_4)/2 - sum_k (sign(c_k) A_k / 2) (F_{k+1} - F_k),
+//   A_k = 1 - (1 - |c_k|) psi(r_k),
+// r_k the density jump across wave k at the upwind face (i-1/2 if c_k > 0,
+// i+3/2 otherwise) over the jump at this face (psi = 0 where that is 0), and
+// psi(r) = limited_slope(r, 1), the limiter of the unsplit schemes in ratio
+// form (minmod -> minbee for theta = 1, van Leer, van Albada, hybrid).
+// Updates [lo, hi) in place (lo >= 2, hi <= n - 2); returns the fluxes
+// through lo - 1/2 and hi - 1/2.
+template <class R>
+inline void waf_row(const Params<R>& P, std::vector<std::array<R, 5>>& u, int lo, int hi, R dtdx, R Flo[5],
+                    R Fhi[5]) {
+  const int n = (int)u.size();
+  std::vector<Side<R>> sd(n);
+  std::vector<Fan<R>> fan(n);
+  std::vector<std::array<R, 5>> FW(n);
+  for (int j = lo - 2; j < hi + 2; ++j) make_side(u[j].data(), P.gas, sd[j]);
+  for (int j = lo - 2; j < hi + 1; ++j) hllc_fan(sd[j], sd[j + 1], P.gas, fan[j]);  // face j + 1/2
+  for (int i = lo - 1; i < hi; ++i) {
+    const Fan<R>& f = fan[i];
+    R F[5];
+    for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (f.F[0][v] + f.F[3][v]);
+    for (int k = 0; k < 3; ++k) {
+      R c = dtdx * f.S[k];
+      R s = c > R(0.0) ? R(1.0) : (c < R(0.0) ? R(-1.0) : R(0.0));
+      const Fan<R>& up = c > R(0.0) ? fan[i - 1] : fan[i + 1];
+      R psi = R(0.0);
+      if (f.drho[k] != R(0.0)) psi = limited_slope(P.limiter, P.theta, up.drho[k] / f.drho[k], R(1.0));
+      R A = R(1.0) - (R(1.0) - fabs(c)) * psi;
+      R w = R(0.5) * s * A;
+      for (int v = 0; v < 5; ++v) F[v] = F[v] - w * (f.F[k + 1][v] - f.F[k][v]);
+    }
+    for (int v = 0; v < 5; ++v) FW[i][v] = F[v];
+  }
+  for (int i = lo; i < hi; ++i)
+    for (int v = 0; v < 5; ++v) u[i][v] = u[i][v] - dtdx * (FW[i][v] - FW[i - 1][v]);
+  for (int v = 0; v < 5; ++v) {
+    Flo[v] = FW[lo - 1][v];
+    Fhi[v] = FW[hi - 1][v];
+  }
+}
+
+template <class R> inline void split_group(const Params<R>& P, const Box& B, const R* Uin, GroupOut<R>& out) {
+  const int N = B.N, g = B.g, M = B.M;
+  const int s = required_ghost(P.scheme, 0);
+  Field5<R> U(B.M3);
+  for (long i = 0; i < B.M3; ++i)
+    for (int v = 0; v < 5; ++v) U(v, i) = Uin[v * B.M3 + i];
+  const int order[3] = {P.split_order ? 2 : 0, 1, P.split_order ? 0 : 2};
+  std::vector<R> FB(out.flux ? 30L * N * N : 0);
+  for (int k = 0; k < 3; ++k) {
+    const int d = order[k];
+    const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;  // transverse axes, e1 < e2
+    // rows the later sweeps read: [-s, N+s) along the axes swept later, [0, N) otherwise
+    auto later = [&](int e) {
+      for (int m = k + 1; m < 3; ++m)
+        if (order[m] == e) return true;
+      return false;
+    };
+    const int a1 = later(e1) ? -s : 0, b1 = later(e1) ? N + s : N;
+    const int a2 = later(e2) ? -s : 0, b2 = later(e2) ? N + s : N;
+    const R dtdx = P.dt / P.dx[d];
+    const R hdtdx = R(0.5) * P.dt / P.dx[d];
+    for (int q2 = a2; q2 < b2; ++q2)
+      for (int q1 = a1; q1 < b1; ++q1) {
+        std::vector<std::array<R, 5>> row(M);
+        int c[3];
+        c[e1] = q1;
+        c[e2] = q2;
+        for (int j = 0; j < M; ++j) {
+          c[d] = j - g;
+          R gl[5];
+          U.get(B.at(c[0], c[1], c[2]), gl);
+          to_local(gl, row[j].data(), d);
+        }
+        R Flo[5], Fhi[5];
+        if (P.scheme == SCH_RTVD)
+          rtvd_row(P, row, g, g + N, dtdx, hdtdx, Flo, Fhi);
+        else
+          waf_row(P, row, g, g + N, dtdx, Flo, Fhi);
+        for (int j = g; j < g + N; ++j) {
+          c[d] = j - g;
+          R gl[5];
+          to_global(row[j].data(), gl, d);
+          U.set(B.at(c[0], c[1], c[2]), gl);
+        }
+        if (out.flux && q1 >= 0 && q1 < N && q2 >= 0 && q2 < N) {
+          R fl[5], fh[5];
+          to_global(Flo, fl, d);
+          to_global(Fhi, fh, d);
+          // [a][b]: a the larger transverse axis (e2), b the smaller (e1)
+          for (int v = 0; v < 5; ++v) {
+            FB[((2 * d) * 5 + v) * N * N + (long)q2 * N + q1] = fl[v];
+            FB[((2 * d + 1) * 5 + v) * N * N + (long)q2 * N + q1] = fh[v];
+          }
+        }
+      }
+    (void)s;
+  }
+  for (int z = 0; z < N; ++z)
+    for (int y = 0; y < N; ++y)
+      for (int x = 0; x < N; ++x) {
+        R Un[5];
+        U.get(B.at(x, y, z), Un);
+        long o = ((long)z * N + y) * N + x;
+        for (int v = 0; v < 5; ++v) out.U_out[(long)v * N * N * N + o] = Un[v];
+        bool nan = false;
+        for (int v = 0; v < 5; ++v) nan = nan || isnan_r(Un[v]);
+        if (nan) out.status |= ST_NAN;
+        if (!(Un[0] > R(0.0))) {
+          out.status |= ST_NEG_DENS;
+        } else {
+          R p = (P.gas.gamma - R(1.0)) * (Un[4] - R(0.5) * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) / Un[0]);
+          if (!(p > R(0.0))) out.status |= ST_NEG_PRES;
+        }
+      }
+  if (out.flux)
+    for (long i = 0; i < 30L * N * N; ++i) out.flux[i] = FB[i];
+}
+
 template <class R> inline void advance_group(const Params<R>& P, const Box& B, const R* Uin, GroupOut<R>& out) {
   switch (P.scheme) {
     case SCH_MHM: mhm_group(P, B, Uin, out); break;
     case SCH_VL: vl_group(P, B, Uin, out); break;
+    case SCH_RTVD:
+    case SCH_WAF: split_group(P, B, Uin, out); break;
     default: ctu_group(P, B, Uin, out); break;
   }
 }
