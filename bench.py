@@ -149,6 +149,7 @@ def time_box(box, steps, warmup, torch, sampler=None):
         ev[k][1].record(s)
         box.swap()
         box.compute_dt(s)
+        box.end_step()
         ev[k][2].record(s)
     t1.record(s)
     torch.cuda.synchronize()
@@ -352,6 +353,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mixed / VL detail lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--quick", action="store_true", help="main line only (no extra, cpu_baseline or e2e legs)")
+    ap.add_argument("--legs", default="all",
+                    help="comma list of extra legs to run: precisions, schemes, amr_levels, amr_hierarchy, "
+                         "serving (default all)")
     ap.add_argument("--block-threads", type=int, default=0,
                     help="use this many threads per CTA for the main line instead of autotuning")
     args = ap.parse_args()
@@ -449,10 +453,12 @@ def main():
         del hs
 
     extra = {}
+    legs = set(args.legs.split(",")) if args.legs != "all" else {"precisions", "schemes", "amr_levels",
+                                                                  "amr_hierarchy", "serving"}
     if not args.no_extra and rank == 0:
         del box
         torch.cuda.empty_cache()
-        for name, prec, k in (("fp64", H.FP64, 4), ("mixed", H.FP32_MIXED, 50)):
+        for name, prec, k in (("fp64", H.FP64, 4), ("mixed", H.FP32_MIXED, 50)) if "precisions" in legs else ():
             bx = RT.UniformBox(U, make_params(H, prec, dx), cfl=CFL, device=dev, stream=stream)
             tb = bx.tune() if prec != H.FP64 else None
             bx.compute_dt()
@@ -464,7 +470,9 @@ def main():
             torch.cuda.empty_cache()
         for tag, sch, rec, rs, ch in (("vl_plm_hllc_fp32", H.VL, H.PLM, H.RS_HLLC, 0),
                                       ("mhm_ppm_roe_fp32", H.MHM, H.PPM, H.RS_ROE, 0),
-                                      ("ctu_ppm_roe_characteristic_fp32", H.CTU, H.PPM, H.RS_ROE, 1)):
+                                      ("ctu_ppm_roe_characteristic_fp32", H.CTU, H.PPM, H.RS_ROE, 1),
+                                      ("rtvd_fp32", H.RTVD, H.PLM, H.RS_HLLC, 0),
+                                      ("waf_hllc_fp32", H.WAF, H.PLM, H.RS_HLLC, 0)) if "schemes" in legs else ():
             p = make_params(H, H.FP32, dx)
             p.scheme, p.recon, p.riemann, p.characteristic = sch, rec, rs, ch
             bx = RT.UniformBox(U, p, cfl=CFL, device=dev, stream=stream)
@@ -475,10 +483,13 @@ def main():
                           "kernel_ms": am, "block_threads": tb["block_threads"]}
             del bx
         torch.cuda.empty_cache()
-        extra["amr_levels"] = amr_leg(H, RT, W, torch, dev)
-        extra["amr_hierarchy"] = amr_hierarchy_leg(H, RT, W, torch, dev)
+        if "amr_levels" in legs:
+            extra["amr_levels"] = amr_leg(H, RT, W, torch, dev)
+        if "amr_hierarchy" in legs:
+            extra["amr_hierarchy"] = amr_hierarchy_leg(H, RT, W, torch, dev)
         torch.cuda.empty_cache()
-        extra["serving"] = serving_leg(H, torch, dev)
+        if "serving" in legs:
+            extra["serving"] = serving_leg(H, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

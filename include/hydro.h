@@ -49,7 +49,8 @@ extern "C" {
 #endif
 
 /* ---- enumerations (Sec. 2) ---------------------------------------------- */
-enum { HYDRO_MHM = 0, HYDRO_VL = 1, HYDRO_CTU = 2 };                 /* scheme   */
+enum { HYDRO_MHM = 0, HYDRO_VL = 1, HYDRO_CTU = 2,                  /* scheme: unsplit */
+       HYDRO_RTVD = 3, HYDRO_WAF = 4 };                                /* split (Sec. 3.2) */
 enum { HYDRO_PLM = 0, HYDRO_PPM = 1 };                               /* recon    */
 enum { HYDRO_LIM_MINMOD = 0, HYDRO_LIM_VANLEER = 1,                  /* limiter  */
        HYDRO_LIM_VANALBADA = 2, HYDRO_LIM_HYBRID = 3 };
@@ -102,6 +103,16 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge
  *                sweep, each wave is reconstructed with the same scalar PLM /
  *                PPM and limiter, and the faces are projected back with the
  *                right eigenvectors.  Same ghost widths.
+ *   split_order  HYDRO_RTVD / HYDRO_WAF only: the sweeps of a step run
+ *                x, y, z (0) or z, y, x (1); alternate them between steps
+ *                (Strang).  The other schemes ignore it.
+ *
+ * The split schemes (the directionally split comparison schemes of Sec.
+ * 3.2): RTVD = relaxing TVD in the flux-split form of Trac & Pen (2003),
+ * freezing speed |u_n| + c_s, first-order half step, limited full step;
+ * WAF = Toro's TVD weighted average flux on the HLLC fan, the limiter
+ * applied to the upwind/local ratio of each wave's density jump.  Both use
+ * `limiter` / `theta`; recon, characteristic and riemann are ignored.
  */
 typedef struct hydro_params {
   int scheme, recon, limiter, riemann, roe_fallback, precision;
@@ -113,10 +124,12 @@ typedef struct hydro_params {
   void* workspace;
   size_t workspace_bytes;
   int characteristic;
+  int split_order;
 } hydro_params;
 
 /* Ghost layers the scheme needs (Sec. 2): MHM and CTU 2 (PLM) / 3 (PPM);
- * VL 3 (PLM) / 4 (PPM).  Returns HYDRO_EINVAL for unknown enums. */
+ * VL 3 (PLM) / 4 (PPM); RTVD 3 and WAF 2 (any recon).  Returns HYDRO_EINVAL
+ * for unknown enums. */
 int hydro_required_ghost(int scheme, int recon);
 
 /* Device scratch (bytes) hydro_advance* needs for this configuration and

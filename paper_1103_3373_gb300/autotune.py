@@ -28,8 +28,8 @@ def _key(p: H.Params, tag):
     dev = torch.cuda.current_device()
     name = torch.cuda.get_device_name(dev)
     lim = "minmod" if p.limiter == H.LIM_MINMOD else "other"
-    return "%s|%d|%d|%d|%d|%d|%d|%s|%s" % (name, p.scheme, p.recon, p.characteristic, p.riemann, p.precision,
-                                          p.roe_fallback, lim, tag)
+    return "%s|%d|%d|%d|%d|%d|%d|%s|%s" % (name, p.scheme, p.recon if p.scheme <= H.CTU else 0,
+                                          p.characteristic, p.riemann, p.precision, p.roe_fallback, lim, tag)
 
 
 def _load_file():

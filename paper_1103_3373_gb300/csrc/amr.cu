@@ -4,10 +4,10 @@
 // fluxes (Sec. 2 step (5), Sec. 4.3) and restriction.
 //
 // All three data kernels are bound by memory traffic, not arithmetic:
-//   prepare   one CTA per (group, padded z-plane), one thread per cell of
-//             the plane: a map lookup, then 5 loads (copy) or 7 x 5 (x2 with
-//             time interpolation) loads of parent cells that neighbouring
-//             threads share through L1/L2;
+//   prepare   one CTA per group, one thread per (x, y) column of the padded
+//             group walking along z: per cell a map lookup, then 5 loads
+//             (copy) or 7 x 5 (x2 with time interpolation) loads of parent
+//             cells that neighbouring threads share through L1/L2;
 //   reflux    one CTA per coarse group; only groups next to a refined one do
 //             any work, one thread per cell of their boundary shell;
 //   restrict  one thread per coarse cell under a fine group: 8 x 5 loads,
@@ -29,6 +29,7 @@ namespace {
 
 constexpr int AN = 16;  // group edge (the only size built)
 constexpr int AMR_THREADS = 256;
+constexpr int AMR_PREP_THREADS = 512;  // >= (N + 2 ghost)^2 for ghost <= 3
 
 struct LevelView {
   const void* U;
@@ -162,44 +163,43 @@ __device__ __forceinline__ void prepare_cell(const LevelView& F, const LevelView
   for (int v = 0; v < 5; ++v) o[v * M3] = acc[v];
 }
 
-// Halo-padded input of every group of F.  CTA (k, c) = (blockIdx.x,
-// blockIdx.y) writes the padded
-// plane c of group k (MG = N + 2 ghost known at compile time, so the cell
-// index arithmetic is by constants); MG = 0 reads the ghost width at run time.
+// Halo-padded input of every group of F.  CTA k fills group k; each thread
+// owns one (x, y) column of the padded group and walks it along z (MG = N + 2
+// ghost known at compile time, so the index arithmetic is by constants; MG = 0
+// reads the ghost width at run time).
 template <class S, int MG>
-__global__ void __launch_bounds__(AMR_THREADS)
+__global__ void __launch_bounds__(AMR_PREP_THREADS)
     amr_prepare_kernel(LevelView F, LevelView C, const S* __restrict__ cnew, S theta, int bc, int ghost,
                        S* __restrict__ out, unsigned* err) {
   const int M = MG ? MG : AN + 2 * ghost;
   const int g = MG ? (MG - AN) / 2 : ghost;
   const long long M3 = (long long)M * M * M;
-  const int k = blockIdx.x;
-  const int c = blockIdx.y;
-  S* base = out + (long long)k * 5 * M3 + (long long)c * M * M;
-  if (!origin_ok(F, k)) {
-    for (int r = threadIdx.x; r < M * M; r += blockDim.x) {
-      if (r == 0) raise_err(err, HYDRO_AMR_ENESTING);
+  for (int k = blockIdx.x; k < F.G; k += gridDim.x) {
+    S* base = out + (long long)k * 5 * M3;
+    if (!origin_ok(F, k)) {
+      if (threadIdx.x == 0) raise_err(err, HYDRO_AMR_ENESTING);
+      for (long long r = threadIdx.x; r < M3; r += blockDim.x)
 #pragma unroll
-      for (int v = 0; v < 5; ++v) base[v * M3 + r] = S(NAN);
+        for (int v = 0; v < 5; ++v) base[v * M3 + r] = S(NAN);
+      continue;
     }
-    return;
-  }
-  for (int r = threadIdx.x; r < M * M; r += blockDim.x) {
-    const int b = r / M, a = r - b * M;
-    prepare_cell<S>(F, C, cnew, theta, bc, g, k, a, b, c, base + r, M3, err);
+    for (int r = threadIdx.x; r < M * M; r += blockDim.x) {
+      const int b = r / M, a = r - b * M;
+      for (int c = 0; c < M; ++c)
+        prepare_cell<S>(F, C, cnew, theta, bc, g, k, a, b, c, base + (long long)c * M * M + r, M3, err);
+    }
   }
 }
 
 template <class S>
 void launch_prepare(const LevelView& F, const LevelView& C, const S* cnew, S theta, int bc, int ghost, S* out,
                     unsigned* err, cudaStream_t st) {
-  const int M = AN + 2 * ghost;
-  dim3 grid(F.G, M);
+  const int grid = F.G < (1 << 20) ? F.G : (1 << 20);
   switch (ghost) {
-    case 2: amr_prepare_kernel<S, AN + 4><<<grid, AMR_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
-    case 3: amr_prepare_kernel<S, AN + 6><<<grid, AMR_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
-    case 4: amr_prepare_kernel<S, AN + 8><<<grid, AMR_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
-    default: amr_prepare_kernel<S, 0><<<grid, AMR_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
+    case 2: amr_prepare_kernel<S, AN + 4><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
+    case 3: amr_prepare_kernel<S, AN + 6><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
+    case 4: amr_prepare_kernel<S, AN + 8><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
+    default: amr_prepare_kernel<S, 0><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
   }
 }
 

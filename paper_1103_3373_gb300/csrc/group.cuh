@@ -35,7 +35,7 @@ struct WorkTable {
 // Launch-wide constants.
 struct KConst {
   double gamma, dens_floor, pres_floor, theta;
-  int limiter, fallback, ghost;
+  int limiter, fallback, ghost, split_order;
   long long ring_elems;  // per-CTA scratch elements (global-memory rings)
 };
 

@@ -80,6 +80,9 @@ void ensure_registered(State& s) {
   hyd_reg_ctu_char_fp64(s.tab);
   hyd_reg_ctu_char_fp32(s.tab);
   hyd_reg_ctu_char_mixed(s.tab);
+  hyd_reg_split_fp64(s.tab);
+  hyd_reg_split_fp32(s.tab);
+  hyd_reg_split_mixed(s.tab);
   s.registered = true;
 }
 
@@ -103,8 +106,8 @@ int device_sms(State& s, int dev) {
 }
 
 bool valid_enums(const hydro_params* p) {
-  return p->scheme >= 0 && p->scheme <= 2 && p->recon >= 0 && p->recon <= 1 && p->limiter >= 0 && p->limiter <= 3 &&
-         (p->characteristic == 0 || p->characteristic == 1) &&
+  return p->scheme >= 0 && p->scheme <= 4 && p->recon >= 0 && p->recon <= 1 && p->limiter >= 0 && p->limiter <= 3 &&
+         (p->characteristic == 0 || p->characteristic == 1) && (p->split_order == 0 || p->split_order == 1) &&
          p->riemann >= 0 && p->riemann <= 3 && p->precision >= 0 && p->precision <= 2 &&
          (p->riemann != HYDRO_RS_ROE ||
           (p->roe_fallback == HYDRO_RS_HLLE || p->roe_fallback == HYDRO_RS_HLLC || p->roe_fallback == HYDRO_RS_EXACT));
@@ -177,6 +180,7 @@ int launch_table(const hydro_params* p, const WorkTable& wt, int N, int ghost, v
   kc.theta = p->theta;
   kc.limiter = p->limiter;
   kc.fallback = p->roe_fallback;
+  kc.split_order = p->split_order;
   kc.ghost = ghost;
   kc.ring_elems = L.k->ring_elems;
   void* ws = p->workspace;
@@ -193,7 +197,9 @@ bool finite_pos(double a) { return a > 0.0 && a < 1e300; }
 extern "C" {
 
 int hydro_required_ghost(int scheme, int recon) {
-  if (scheme < 0 || scheme > 2 || recon < 0 || recon > 1) return HYDRO_EINVAL;
+  if (scheme < 0 || scheme > 4 || recon < 0 || recon > 1) return HYDRO_EINVAL;
+  if (scheme == HYDRO_RTVD) return 3;
+  if (scheme == HYDRO_WAF) return 2;
   int s = recon == HYDRO_PPM ? 2 : 1;
   return scheme == HYDRO_VL ? s + 2 : s + 1;
 }

@@ -7,6 +7,7 @@
 #pragma once
 #include "ctu.cuh"
 #include "mhm.cuh"
+#include "split.cuh"
 #include "vl.cuh"
 
 namespace hyd {
@@ -16,21 +17,24 @@ template <int SCH, int REC, int PR, int N> struct KTraits {
   using T = typename P::T;
   using S = typename P::S;
   static constexpr int S_ = REC == PPM ? 2 : 1;
-  static constexpr int RING = SCH == CTU ? CtuLayout<N, S_>::TOTAL
+  static constexpr int MS = N + 2 * SplitGhost<SCH>::value;  // padded edge of the split schemes
+  static constexpr int RING = SCH == CTU   ? CtuLayout<N, S_>::TOTAL
                               : SCH == MHM ? MhmLayout<N, S_>::TOTAL
-                                           : VlLayout<N, S_>::TOTAL;
+                              : SCH == VL  ? VlLayout<N, S_>::TOTAL
+                                           : 5 * MS * MS * MS;
   static constexpr bool SMEM = PR != P_FP64;  // FP64 rings do not fit in shared memory
 };
 
 // Largest CTA: FP64 kernels need up to 255 registers per thread; the FP32
 // kernels run 16 warps per SM (128 registers per thread) except the exact
-// solver, whose Newton iteration needs more registers.
-template <int PR, int RS> struct MaxThreads {
-  static constexpr int value = PR == P_FP64 ? 256 : (RS == RS_EXACT ? 384 : 512);
+// solver, whose Newton iteration needs more registers, and the split
+// schemes, whose threads each carry a row's sliding window.
+template <int PR, int RS, int SCH = 0> struct MaxThreads {
+  static constexpr int value = PR == P_FP64 ? 256 : ((RS == RS_EXACT || SCH >= SCH_RTVD) ? 384 : 512);
 };
 
 template <int SCH, int REC, int RS, int PR, int N, bool CH>
-__global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
+__global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
     advance_kernel(const __grid_constant__ WorkTable wt, const KConst kc, void* ws) {
   using Tr = KTraits<SCH, REC, PR, N>;
   using T = typename Tr::T;
@@ -52,6 +56,7 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
   o.theta = (T)kc.theta;
   o.limiter = kc.limiter;
   o.fallback = kc.fallback;
+  o.split_order = kc.split_order;
   if (threadIdx.x < CHAIN_MAX) sts[threadIdx.x] = 0;
   const int b = blockIdx.x;
   const int per = wt.total / gridDim.x, extra = wt.total % gridDim.x;
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
     const SegDesc& sg = wt.seg[s];
     const int gi = w - sg.first;
     int K = 1;
-    if (sg.mode == 1) {
+    if (sg.mode == 1 && SCH <= CTU) {
       const int left = sg.GZ - gi % sg.GZ;  // groups left in this column
       K = wend - w < left ? wend - w : left;
       K = K < CHAIN_MAX ? K : CHAIN_MAX;
@@ -76,8 +81,10 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS>::value, 1)
       ctu_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
     else if constexpr (SCH == MHM)
       mhm_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
-    else
+    else if constexpr (SCH == VL)
       vl_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
+    else
+      split_group<T, S, MIXED, SCH, N>(C, o, ring, sts);
     __syncthreads();
     if (threadIdx.x < K) {
       if (sg.status) sg.status[C.user_index(threadIdx.x)] = sts[threadIdx.x];
@@ -97,7 +104,7 @@ struct KernelEntry {
 };
 
 // (scheme, reconstruction, characteristic, solver, precision)
-constexpr int NKEY = 3 * 2 * 2 * 4 * 3;
+constexpr int NKEY = 5 * 2 * 2 * 4 * 3;
 inline int kernel_key(int sch, int rec, int ch, int rs, int pr) {
   return (((sch * 2 + rec) * 2 + ch) * 4 + rs) * 3 + pr;
 }
@@ -108,7 +115,7 @@ template <int SCH, int REC, int RS, int PR, int N, bool CH> inline void put_kern
   e.fn = (const void*)&advance_kernel<SCH, REC, RS, PR, N, CH>;
   e.ring_elems = Tr::RING;
   e.elem_bytes = (int)sizeof(typename Tr::T);
-  e.max_threads = MaxThreads<PR, RS>::value;
+  e.max_threads = MaxThreads<PR, RS, SCH>::value;
   e.smem = Tr::SMEM ? 1 : 0;
 }
 
@@ -121,6 +128,16 @@ template <int SCH, int PR, int N, bool CH> inline void put_scheme(KernelEntry* t
   put_kernel<SCH, PPM, RS_HLLE, PR, N, CH>(tab);
   put_kernel<SCH, PPM, RS_HLLC, PR, N, CH>(tab);
   put_kernel<SCH, PPM, RS_ROE, PR, N, CH>(tab);
+}
+
+// The split schemes ignore reconstruction, characteristic and solver: one
+// kernel serves every key of (scheme, precision).
+template <int SCH, int PR, int N> inline void put_split(KernelEntry* tab) {
+  put_kernel<SCH, PLM, RS_HLLC, PR, N, false>(tab);
+  const KernelEntry e = tab[kernel_key(SCH, PLM, 0, RS_HLLC, PR)];
+  for (int rec = 0; rec < 2; ++rec)
+    for (int ch = 0; ch < 2; ++ch)
+      for (int rs = 0; rs < 4; ++rs) tab[kernel_key(SCH, rec, ch, rs, PR)] = e;
 }
 
 }  // namespace hyd
@@ -146,3 +163,6 @@ HYD_DECLARE_REG(hyd_reg_vl_char_mixed);
 HYD_DECLARE_REG(hyd_reg_ctu_char_fp64);
 HYD_DECLARE_REG(hyd_reg_ctu_char_fp32);
 HYD_DECLARE_REG(hyd_reg_ctu_char_mixed);
+HYD_DECLARE_REG(hyd_reg_split_fp64);
+HYD_DECLARE_REG(hyd_reg_split_fp32);
+HYD_DECLARE_REG(hyd_reg_split_mixed);

@@ -51,6 +51,7 @@ template <class T> struct Opts {
   T theta;
   int limiter;
   int fallback;
+  int split_order;  // split schemes: sweeps x, y, z (0) or z, y, x (1)
 };
 
 template <class T> __device__ __forceinline__ T absv(T a) { return a < T(0) ? -a : a; }

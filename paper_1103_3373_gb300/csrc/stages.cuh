@@ -45,99 +45,110 @@ template <class T, int N, int DXY, int DZ> struct FaceRings {
   }
 };
 
-// Final Riemann solves of chain plane p (0 <= p <= NP, NP = K N): x and y
-// faces of the interior cells of plane p (if p < NP) and the z faces between
-// planes p-1 and p.  Fluxes on a group boundary are stored at once (step
-// (5)); a z face between two groups of a chain is the +z face of the lower
-// and the -z face of the upper one.
+// One final Riemann solve of chain plane p (0 <= p <= NP, NP = K N), item
+// idx of 2 nx + N^2 (nx = N (N+1) if p < NP, else 0): the x faces, then the
+// y faces of the interior cells of plane p, then the z faces between planes
+// p-1 and p.  Fluxes on a group boundary are stored at once (step (5)); a z
+// face between two groups of a chain is the +z face of the lower and the -z
+// face of the upper one.
 template <class T, class S, bool MIXED, int RS, int N, class FR>
-__device__ __forceinline__ void stage_flux2(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
-                                            unsigned* sts) {
+__device__ __forceinline__ void flux2_item(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+                                           unsigned* sts, int idx, int nx) {
   constexpr int LL = FR::LL;
-  const int NP = K * N;
-  const int nx = (p < NP) ? N * (N + 1) : 0;
-  const int cnt = 2 * nx + N * N;
   const int pk = p / N;  // chain group of plane p (K for the top face)
-  for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-    const T *pl, *pr;
-    T* pf;
-    int d, fs, bface = -1, ba = 0, bb = 0;
-    if (idx < nx) {
-      int j = idx / (N + 1), f = idx - j * (N + 1);
-      d = 0;
-      pl = &R.XY(p, 0, 1, 0, j + 1, f);
-      pr = &R.XY(p, 0, 0, 0, j + 1, f + 1);
-      pf = &R.F2x(p, 0, j, f);
-      fs = N * (N + 1);
-      if (f == 0 || f == N) {
-        bface = f == 0 ? 0 : 1;
-        ba = p - pk * N;
-        bb = j;
-      }
-    } else if (idx < 2 * nx) {
-      int k = idx - nx;
-      int f = k / N, i = k - f * N;
-      d = 1;
-      pl = &R.XY(p, 1, 1, 0, f, i + 1);
-      pr = &R.XY(p, 1, 0, 0, f + 1, i + 1);
-      pf = &R.F2y(p, 0, f, i);
-      fs = (N + 1) * N;
-      if (f == 0 || f == N) {
-        bface = f == 0 ? 2 : 3;
-        ba = p - pk * N;
-        bb = i;
-      }
-    } else {
-      int k = idx - 2 * nx;
-      int j = k / N, i = k - j * N;
-      d = 2;
-      pl = &R.Zs(p - 1, 1, 0, j + 1, i + 1);
-      pr = &R.Zs(p, 0, 0, j + 1, i + 1);
-      pf = &R.F2z(p, 0, j, i);
-      fs = N * N;
-      if (p == pk * N) {
-        bface = 4;
-        ba = j;
-        bb = i;
-      }
+  const T *pl, *pr;
+  T* pf;
+  int d, fs, bface = -1, ba = 0, bb = 0;
+  if (idx < nx) {
+    int j = idx / (N + 1), f = idx - j * (N + 1);
+    d = 0;
+    pl = &R.XY(p, 0, 1, 0, j + 1, f);
+    pr = &R.XY(p, 0, 0, 0, j + 1, f + 1);
+    pf = &R.F2x(p, 0, j, f);
+    fs = N * (N + 1);
+    if (f == 0 || f == N) {
+      bface = f == 0 ? 0 : 1;
+      ba = p - pk * N;
+      bb = j;
     }
-    const LocalComps lc(d);
-    T UL[5], UR[5], F[5];
-    load_local(pl, LL, lc, UL);
-    load_local(pr, LL, lc, UR);
-    const unsigned s = riemann_local<T, MIXED, RS>(UL, UR, o, F);
-    store_local(pf, fs, lc, F);
-    mark_status<N>(sts, K, p, 0, d == 2 ? 1 : 0, s);
-    if (bface >= 0) {
-      const int gv[5] = {0, lc.c1, lc.c2, lc.c3, 4};
+  } else if (idx < 2 * nx) {
+    int k = idx - nx;
+    int f = k / N, i = k - f * N;
+    d = 1;
+    pl = &R.XY(p, 1, 1, 0, f, i + 1);
+    pr = &R.XY(p, 1, 0, 0, f + 1, i + 1);
+    pf = &R.F2y(p, 0, f, i);
+    fs = (N + 1) * N;
+    if (f == 0 || f == N) {
+      bface = f == 0 ? 2 : 3;
+      ba = p - pk * N;
+      bb = i;
+    }
+  } else {
+    int k = idx - 2 * nx;
+    int j = k / N, i = k - j * N;
+    d = 2;
+    pl = &R.Zs(p - 1, 1, 0, j + 1, i + 1);
+    pr = &R.Zs(p, 0, 0, j + 1, i + 1);
+    pf = &R.F2z(p, 0, j, i);
+    fs = N * N;
+    if (p == pk * N) {
+      bface = 4;
+      ba = j;
+      bb = i;
+    }
+  }
+  const LocalComps lc(d);
+  T UL[5], UR[5], F[5];
+  load_local(pl, LL, lc, UL);
+  load_local(pr, LL, lc, UR);
+  const unsigned s = riemann_local<T, MIXED, RS>(UL, UR, o, F);
+  store_local(pf, fs, lc, F);
+  mark_status<N>(sts, K, p, 0, d == 2 ? 1 : 0, s);
+  if (bface >= 0) {
+    const int gv[5] = {0, lc.c1, lc.c2, lc.c3, 4};
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        if (bface < 4) {
-          C.store_flux(pk, bface, gv[k], ba, bb, F[k]);
-        } else {
-          if (pk < K) C.store_flux(pk, 4, gv[k], ba, bb, F[k]);
-          if (pk > 0) C.store_flux(pk - 1, 5, gv[k], ba, bb, F[k]);
-        }
+    for (int k = 0; k < 5; ++k) {
+      if (bface < 4) {
+        C.store_flux(pk, bface, gv[k], ba, bb, F[k]);
+      } else {
+        if (pk < K) C.store_flux(pk, 4, gv[k], ba, bb, F[k]);
+        if (pk > 0) C.store_flux(pk - 1, 5, gv[k], ba, bb, F[k]);
       }
     }
   }
 }
 
-// Conservative update of chain plane p from the final fluxes (step (4)).
+// All final Riemann solves of chain plane p, over the CTA's threads.
+template <class T, class S, bool MIXED, int RS, int N, class FR>
+__device__ __forceinline__ void stage_flux2(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+                                            unsigned* sts) {
+  const int nx = (p < K * N) ? N * (N + 1) : 0;
+  const int cnt = 2 * nx + N * N;
+  for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) flux2_item<T, S, MIXED, RS, N>(C, o, R, p, K, sts, idx, nx);
+}
+
+// Conservative update of cell idx (of N^2) of chain plane p from the final
+// fluxes (step (4)).
+template <class T, class S, bool MIXED, int N, class FR>
+__device__ __forceinline__ void update_item(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+                                            unsigned* sts, int idx) {
+  int j = idx / N, i = idx - j * N;
+  T dF[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    dF[0][v] = R.F2x(p, v, j, i + 1) - R.F2x(p, v, j, i);
+    dF[1][v] = R.F2y(p, v, j + 1, i) - R.F2y(p, v, j, i);
+    dF[2][v] = R.F2z(p + 1, v, j, i) - R.F2z(p, v, j, i);
+  }
+  mark_status<N>(sts, K, p, 0, 0, update_cell<T, S, MIXED, N>(C, i, j, p, dF, o.gas));
+}
+
+// Conservative update of chain plane p, over the CTA's threads.
 template <class T, class S, bool MIXED, int N, class FR>
 __device__ __forceinline__ void stage_update(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
                                              unsigned* sts) {
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    int j = idx / N, i = idx - j * N;
-    T dF[3][5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      dF[0][v] = R.F2x(p, v, j, i + 1) - R.F2x(p, v, j, i);
-      dF[1][v] = R.F2y(p, v, j + 1, i) - R.F2y(p, v, j, i);
-      dF[2][v] = R.F2z(p + 1, v, j, i) - R.F2z(p, v, j, i);
-    }
-    mark_status<N>(sts, K, p, 0, 0, update_cell<T, S, MIXED, N>(C, i, j, p, dF, o.gas));
-  }
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) update_item<T, S, MIXED, N>(C, o, R, p, K, sts, idx);
 }
 
 // Ring of LW x LW input planes; the plane's lateral index ii maps to the

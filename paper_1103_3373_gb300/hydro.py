@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhydro.so")
 
 # enumerations (include/hydro.h; Sec. 2 of the paper)
-MHM, VL, CTU = 0, 1, 2
+MHM, VL, CTU, RTVD, WAF = 0, 1, 2, 3, 4
 PLM, PPM = 0, 1
 LIM_MINMOD, LIM_VANLEER, LIM_VANALBADA, LIM_HYBRID = 0, 1, 2, 3
 RS_EXACT, RS_HLLE, RS_HLLC, RS_ROE = 0, 1, 2, 3
@@ -27,7 +27,7 @@ ST_ERROR_MASK = ST_NEG_DENS | ST_NEG_PRES | ST_NAN | ST_EXACT_FAIL
 MAX_LEVELS = 32
 AMR_ENESTING, AMR_EDUPLICATE, AMR_EOCTET = 1, 2, 4  # include/hydro_amr.h dev_error bits
 
-SCHEMES = {"mhm": MHM, "vl": VL, "ctu": CTU}
+SCHEMES = {"mhm": MHM, "vl": VL, "ctu": CTU, "rtvd": RTVD, "waf": WAF}
 RECONS = {"plm": PLM, "ppm": PPM}
 SOLVERS = {"exact": RS_EXACT, "hlle": RS_HLLE, "hllc": RS_HLLC, "roe": RS_ROE}
 LIMITERS = {"minmod": LIM_MINMOD, "vanleer": LIM_VANLEER, "vanalbada": LIM_VANALBADA, "hybrid": LIM_HYBRID}
@@ -50,7 +50,7 @@ class _CParams(ctypes.Structure):
                 ("dx", ctypes.c_double * 3), ("dens_floor", ctypes.c_double), ("pres_floor", ctypes.c_double),
                 ("dt_dev", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("characteristic", ctypes.c_int)]
+                ("characteristic", ctypes.c_int), ("split_order", ctypes.c_int)]
 
 
 class _CLevel(ctypes.Structure):
@@ -85,11 +85,12 @@ class Params:
     grid_ctas: int = 0
     workspace: object = None
     characteristic: int = 0  # 1: PLM / PPM on characteristic variables (Sec. 2)
+    split_order: int = 0     # RTVD / WAF: sweeps x, y, z (0) or z, y, x (1)
 
     def c(self):
         p = _CParams()
         for k in ("scheme", "recon", "limiter", "riemann", "roe_fallback", "precision", "block_threads",
-                  "grid_ctas", "characteristic"):
+                  "grid_ctas", "characteristic", "split_order"):
             setattr(p, k, int(getattr(self, k)))
         for k in ("theta", "gamma", "dt", "dens_floor", "pres_floor"):
             setattr(p, k, float(getattr(self, k)))

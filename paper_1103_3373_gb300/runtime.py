@@ -63,10 +63,17 @@ class UniformBox:
     def swap(self):
         self.a, self.b = self.b, self.a
 
+    def end_step(self):
+        """Host-side bookkeeping after a step: the split schemes alternate
+        their sweep order (Strang)."""
+        if self.p.scheme >= H.RTVD:
+            self.p.split_order ^= 1
+
     def step(self, stream=None):
         self.advance(stream)
         self.swap()
         self.compute_dt(stream)
+        self.end_step()
 
     def state(self):
         return self.a
