@@ -361,9 +361,8 @@ def main():
     args = ap.parse_args()
     if args.quick:
         args.no_extra = args.no_cpu = True
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1103_3373_gb300 import replicas
+    rank, world, local = replicas.rank_info()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 
@@ -400,14 +399,11 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     step_ms, adv_ms, total_ms, clocks = time_box(box, args.steps, args.warmup, torch, sampler)
-    if dist:
-        dist.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # every rank advanced its own box (replicas): whole-job rate over the
+    # slowest rank's time
+    value, total_ms, _ = replicas.job_rate(total_ms, cells * args.steps, dist, device=dev)
     st = box.status.cpu().numpy()
     finite = bool(torch.isfinite(box.state()).all().item())
-    value = world * cells * args.steps / (total_ms / 1e3)
 
     # roofline of the dominant kernel (the fused CTU group update)
     with open(os.path.join(ROOT, "paper_1103_3373_gb300", "data", "flops_per_cell.json")) as fh:

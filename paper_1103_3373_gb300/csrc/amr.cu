@@ -191,15 +191,146 @@ __global__ void __launch_bounds__(AMR_PREP_THREADS)
   }
 }
 
-template <class S>
-void launch_prepare(const LevelView& F, const LevelView& C, const S* cnew, S theta, int bc, int ghost, S* out,
-                    unsigned* err, cudaStream_t st) {
+// Coarse window a fine group's padded region (ghost G) and its
+// interpolation stencil need: cells o/2 - LO_OFF + [0, CB) per axis.
+template <int G> struct StageBox {
+  static constexpr int LO_OFF = (G + 1) / 2 + 1;
+  static constexpr int CB = AN / 2 + (G - 1) / 2 + (G + 1) / 2 + 3;
+  static constexpr int CB3 = CB * CB * CB;
+};
+
+// Halo-padded input of every group of F, parents staged in shared memory.
+// CTA k fills group k.  If every padded cell lies in a group of F (the 26
+// neighbour slots are all present) the group is copied; otherwise the
+// parent cells of its padded region and their stencil (the StageBox window,
+// at time theta) are first staged in shared memory, each from its wrapped /
+// clamped coarse cell, and the cells outside F interpolate from there:
+// ((Uc + qx) + qy) + qz with the same operations and order as prepare_cell.
+// Indexing the window by the unwrapped fine coordinate gives the same parent
+// and neighbours as the wrapped one (periodic); at an outflow edge both give
+// a zero slope along the clamped axis.
+template <class S, int G>
+__global__ void __launch_bounds__(AMR_PREP_THREADS)
+    amr_prepare_staged(LevelView F, LevelView C, const S* __restrict__ cnew, S theta, int bc, S* __restrict__ out,
+                       unsigned* err) {
+  constexpr int M = AN + 2 * G;
+  constexpr long long M3 = (long long)M * M * M;
+  constexpr long long N3 = (long long)AN * AN * AN;
+  constexpr int CB = StageBox<G>::CB, CB3 = StageBox<G>::CB3, LO = StageBox<G>::LO_OFF;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  S* cs = reinterpret_cast<S*>(smraw);  // [5][CB3] parent values at time theta
+  unsigned char* okp = smraw + (size_t)5 * CB3 * sizeof(S);
+  __shared__ int need;
+  const S* Uf = (const S*)F.U;
+  for (int k = blockIdx.x; k < F.G; k += gridDim.x) {
+    S* base = out + (long long)k * 5 * M3;
+    if (!origin_ok(F, k)) {  // uniform across the CTA
+      if (threadIdx.x == 0) raise_err(err, HYDRO_AMR_ENESTING);
+      for (long long r = threadIdx.x; r < M3; r += blockDim.x)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) base[v * M3 + r] = S(NAN);
+      continue;
+    }
+    const int ox = F.origin[3 * k], oy = F.origin[3 * k + 1], oz = F.origin[3 * k + 2];
+    if (threadIdx.x == 0) need = 0;
+    __syncthreads();
+    if (threadIdx.x < 27) {
+      const int sx = threadIdx.x % 3 - 1, sy = (threadIdx.x / 3) % 3 - 1, sz = threadIdx.x / 9 - 1;
+      const int fx = amr_cell(ox + (sx < 0 ? -1 : (sx > 0 ? AN : 0)), F.X, bc);
+      const int fy = amr_cell(oy + (sy < 0 ? -1 : (sy > 0 ? AN : 0)), F.Y, bc);
+      const int fz = amr_cell(oz + (sz < 0 ? -1 : (sz > 0 ? AN : 0)), F.Z, bc);
+      if (group_at(F, fx, fy, fz) < 0) atomicOr(&need, 1);
+    }
+    __syncthreads();
+    const int cx0 = (ox >> 1) - LO, cy0 = (oy >> 1) - LO, cz0 = (oz >> 1) - LO;
+    if (need) {
+      for (int idx = threadIdx.x; idx < CB3; idx += blockDim.x) {
+        const int i = idx % CB, j = (idx / CB) % CB, l = idx / (CB * CB);
+        S u[5];
+        const bool present = C.U != nullptr && parent_at(C, cnew, theta, amr_cell(cx0 + i, F.X / 2, bc),
+                                                         amr_cell(cy0 + j, F.Y / 2, bc),
+                                                         amr_cell(cz0 + l, F.Z / 2, bc), u);
+        okp[idx] = present ? 1 : 0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cs[v * CB3 + idx] = present ? u[v] : S(0);
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < M * M; r += blockDim.x) {
+      const int b = r / M, a = r - b * M;
+      const int fu = ox + a - G, fv = oy + b - G;  // unwrapped fine x, y
+      const int fx = amr_cell(fu, F.X, bc), fy = amr_cell(fv, F.Y, bc);
+      for (int c = 0; c < M; ++c) {
+        const int fw = oz + c - G;
+        const int fz = amr_cell(fw, F.Z, bc);
+        S* o = base + (long long)c * M * M + r;
+        const int g = group_at(F, fx, fy, fz);
+        if (g >= 0) {
+          const S* s = Uf + (long long)g * 5 * N3 + ((fz % AN) * AN + fy % AN) * AN + fx % AN;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) o[v * M3] = s[v * N3];
+          continue;
+        }
+        const int ci = (fu >> 1) - cx0, cj = (fv >> 1) - cy0, ck = (fw >> 1) - cz0;  // 1 .. CB-2
+        const int idx = (ck * CB + cj) * CB + ci;
+        const int st[3] = {1, CB, CB * CB};
+        bool ok = okp[idx] != 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ok = ok && okp[idx + st[d]] != 0 && okp[idx - st[d]] != 0;
+        S acc[5];
+        if (ok) {
+          const int fc[3] = {fx, fy, fz};
+#pragma unroll
+          for (int v = 0; v < 5; ++v) acc[v] = cs[v * CB3 + idx];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const S q = (fc[d] & 1) ? S(0.25) : S(-0.25);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              const S uc = cs[v * CB3 + idx];
+              const S uu = cs[v * CB3 + idx + st[d]];
+              const S ud = cs[v * CB3 + idx - st[d]];
+              acc[v] = acc[v] + q * minmod(uu - uc, uc - ud);
+            }
+          }
+        } else {
+          raise_err(err, HYDRO_AMR_ENESTING);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) acc[v] = S(NAN);
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) o[v * M3] = acc[v];
+      }
+    }
+    __syncthreads();  // the window is reused by the CTA's next group
+  }
+}
+
+template <class S, int G>
+cudaError_t launch_staged(const LevelView& F, const LevelView& C, const S* cnew, S theta, int bc, S* out,
+                          unsigned* err, cudaStream_t st) {
+  const size_t smem = (size_t)5 * StageBox<G>::CB3 * sizeof(S) + StageBox<G>::CB3;
+  cudaError_t e = cudaFuncSetAttribute(amr_prepare_staged<S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
   const int grid = F.G < (1 << 20) ? F.G : (1 << 20);
+  amr_prepare_staged<S, G><<<grid, AMR_PREP_THREADS, smem, st>>>(F, C, cnew, theta, bc, out, err);
+  return cudaSuccess;
+}
+
+template <class S>
+cudaError_t launch_prepare(const LevelView& F, const LevelView& C, const S* cnew, S theta, int bc, int ghost,
+                           S* out, unsigned* err, cudaStream_t st) {
   switch (ghost) {
-    case 2: amr_prepare_kernel<S, AN + 4><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
-    case 3: amr_prepare_kernel<S, AN + 6><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
-    case 4: amr_prepare_kernel<S, AN + 8><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
-    default: amr_prepare_kernel<S, 0><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err); break;
+    case 1: return launch_staged<S, 1>(F, C, cnew, theta, bc, out, err, st);
+    case 2: return launch_staged<S, 2>(F, C, cnew, theta, bc, out, err, st);
+    case 3: return launch_staged<S, 3>(F, C, cnew, theta, bc, out, err, st);
+    case 4: return launch_staged<S, 4>(F, C, cnew, theta, bc, out, err, st);
+    default: {
+      const int grid = F.G < (1 << 20) ? F.G : (1 << 20);
+      amr_prepare_kernel<S, 0><<<grid, AMR_PREP_THREADS, 0, st>>>(F, C, cnew, theta, bc, ghost, out, err);
+      return cudaSuccess;
+    }
   }
 }
 
@@ -396,10 +527,12 @@ int hydro_amr_prepare(const hydro_amr_level* fine, const hydro_amr_level* coarse
   if (!U_out) return HYDRO_EINVAL;
   LevelView F = view(fine), C = view(coarse);
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == HYDRO_FP64)
-    launch_prepare<double>(F, C, (const double*)coarse_new, theta, bc, ghost, (double*)U_out, dev_error, st);
-  else
-    launch_prepare<float>(F, C, (const float*)coarse_new, (float)theta, bc, ghost, (float*)U_out, dev_error, st);
+  cudaError_t e =
+      precision == HYDRO_FP64
+          ? launch_prepare<double>(F, C, (const double*)coarse_new, theta, bc, ghost, (double*)U_out, dev_error, st)
+          : launch_prepare<float>(F, C, (const float*)coarse_new, (float)theta, bc, ghost, (float*)U_out, dev_error,
+                                  st);
+  if (e != cudaSuccess) return hyd::record_cuda_error(e);
   return launched();
 }
 

@@ -204,3 +204,26 @@ def test_missing_parent_cell_sets_the_nesting_bit():
     assert np.isfinite(o[0, :, 3:3 + N, 3:3 + N, 3:3 + N]).all()  # the interior is copied
     with pytest.raises(A.NestingError):
         A.prepare(dict(l2), dict(l1), None, 0.0, ghost=3)
+
+
+@pytest.mark.parametrize("scheme,prec", [(O.WAF, H.FP64), (O.RTVD, H.FP32)])
+def test_hierarchy_step_split_scheme_outflow(scheme, prec):
+    """A directionally split scheme inside a 2-level hierarchy with outflow
+    box edges (the refined octet next to the low-x edge): one step against
+    oracle.amr.amr_step."""
+    torch = _torch()
+    levels = _quantised_levels(W.amr_hierarchy(48, (0.25,), center=(0.2, 0.5, 0.6)), prec)
+    assert len(levels) == 2
+    po, ph = params_pair(scheme, O.PLM, O.HLLC, prec, 0.0, (1, 1, 1))
+    dt0 = 0.3 * levels[0]["dx"][0] / 3.0
+    ref = A.amr_step(levels, po, dt0, bc=1)
+    hier = RT.AmrHierarchy(levels, ph, bc=H.BC_OUTFLOW)
+    hier.step(dt0)
+    torch.cuda.synchronize()
+    for l in range(2):
+        got = hier.cur[l].double().cpu().numpy()
+        if prec == H.FP64:
+            np.testing.assert_array_equal(got, ref[l])
+        else:
+            assert rel_l1(got, ref[l]) <= TOL_FP32
+    assert hier.errors() == 0
