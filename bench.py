@@ -352,6 +352,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mixed / VL detail lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--e2e-slabs", type=int, default=8,
+                    help="z-slabs of the end-to-end pipeline (1: copy in, step, copy out in series)")
+    ap.add_argument("--e2e-sweep", default="", help="also time the end-to-end step at these slab counts (1,2,4,...)")
     ap.add_argument("--quick", action="store_true", help="main line only (no extra, cpu_baseline or e2e legs)")
     ap.add_argument("--legs", default="all",
                     help="comma list of extra legs to run: precisions, schemes, amr_levels, amr_hierarchy, "
@@ -428,25 +431,38 @@ def main():
                 "hbm_frac_of_measured": (40.0 * cells + 30.0 * 4 * 256 * 4096) / (adv_ms / 1e3) / 1e9 /
                                         peaks.get("hbm_gbs", 6775.3)}
 
-    # end to end through host buffers (pinned), same metric
+    # end to end through host buffers (pinned), same metric: the slab
+    # pipeline (copies overlapped with the solver, Sec. 4.1), and the serial
+    # form (copy in, step, copy out) for context
     e2e = None
     if not args.quick:
-        hs = RT.HostBoxStepper(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev)
-        ke = max(5, min(args.steps, 50))
-        for _ in range(3):
-            hs.step()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(ke):
-            hs.step()
-        b.record()
-        torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b)
-        e2e = {"value": world * cells * ke / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": hs.h2d_bytes,
-               "d2h_bytes_per_step": hs.d2h_bytes, "steps": ke, "ms_per_step": e_ms / ke}
-        del hs
+        def e2e_run(slabs):
+            hs = RT.HostBoxStepper(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev, slabs=slabs)
+            ke = max(5, min(args.steps, 50))
+            for _ in range(3):
+                hs.step()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(ke):
+                hs.step()
+            b.record()
+            torch.cuda.synchronize()
+            e_ms = a.elapsed_time(b)
+            out = {"value": world * cells * ke / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": hs.h2d_bytes,
+                   "d2h_bytes_per_step": hs.d2h_bytes, "steps": ke, "ms_per_step": e_ms / ke, "slabs": hs.slabs}
+            del hs
+            return out
+        e2e = e2e_run(args.e2e_slabs)
+        if args.e2e_slabs > 1:
+            s = e2e_run(1)
+            e2e["serial"] = {"value": s["value"], "ms_per_step": s["ms_per_step"]}
+        if args.e2e_sweep:
+            e2e["sweep"] = []
+            for S in (int(x) for x in args.e2e_sweep.split(",")):
+                s = e2e_run(S)
+                e2e["sweep"].append({"slabs": s["slabs"], "value": s["value"], "ms_per_step": s["ms_per_step"]})
 
     extra = {}
     legs = set(args.legs.split(",")) if args.legs != "all" else {"precisions", "schemes", "amr_levels",

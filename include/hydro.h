@@ -181,6 +181,22 @@ int hydro_gather_uniform(const void* field, int X, int Y, int Z, int bc, const i
 int hydro_advance_uniform(const hydro_params* p, const void* field_in, void* field_out, int X, int Y, int Z, int N,
                           int bc, void* flux, unsigned* dev_status, void* stream);
 
+/*
+ * hydro_advance_uniform_zrange — hydro_advance_uniform restricted to the
+ * groups whose interior lies in z_begin <= z < z_end (multiples of N): the
+ * halos are still read from the whole field_in (periodic / outflow as bc),
+ * only those groups' cells of field_out, flux and dev_status (full-box group
+ * order) are written.  Lets a caller overlap the host transfers of one z-slab
+ * with the computation of another (Sec. 4.1, asynchronous memory copy).
+ * z_begin and z_end must be multiples of N with 0 <= z_begin <= z_end <= Z
+ * (else HYDRO_EINVAL, checked before any device work); z_begin == z_end is a
+ * no-op.  Slabs of one step may run concurrently on several streams provided
+ * each launch has its own workspace (FP64 forms); they write disjoint cells.
+ */
+int hydro_advance_uniform_zrange(const hydro_params* p, const void* field_in, void* field_out, int X, int Y, int Z,
+                                 int N, int bc, int z_begin, int z_end, void* flux, unsigned* dev_status,
+                                 void* stream);
+
 /* One entry of a multi-level (or multi-box) batch. */
 typedef struct hydro_level {
   const void* U_in;     /* groups [G][5][M^3] (mode 0) or field [5][Z][Y][X] (mode 1) */

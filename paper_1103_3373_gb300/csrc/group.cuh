@@ -18,6 +18,7 @@ struct SegDesc {
   double dt;
   double dx[3];
   int G, mode, bc, X, Y, Z, GX, GY, GZ;
+  int gz0;              // mode 1: first group layer of the entry (its GZ layers follow)
   int first;            // flat index of this entry's first group
 };
 
@@ -84,7 +85,7 @@ template <class T, class S, int N> struct GroupCtx {
       Y = sg.Y;
       Z = sg.Z;
       XYZ = (long long)X * Y * Z;
-      int gz = gi % sg.GZ;
+      int gz = sg.gz0 + gi % sg.GZ;
       int col = gi / sg.GZ;
       int gx = col % sg.GX;
       int gy = col / sg.GX;

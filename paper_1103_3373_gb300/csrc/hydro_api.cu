@@ -285,6 +285,46 @@ int hydro_advance_uniform(const hydro_params* p, const void* field_in, void* fie
   return launch_table(p, wt, N, hydro_required_ghost(p->scheme, p->recon), stream);
 }
 
+int hydro_advance_uniform_zrange(const hydro_params* p, const void* field_in, void* field_out, int X, int Y, int Z,
+                                 int N, int bc, int z_begin, int z_end, void* flux, unsigned* dev_status,
+                                 void* stream) {
+  if (!p || !valid_enums(p) || !valid_physics(p)) return HYDRO_EINVAL;
+  if (N != 16) return HYDRO_EUNSUPPORTED;
+  if (X <= 0 || Y <= 0 || Z <= 0 || X % N || Y % N || Z % N) return HYDRO_EINVAL;
+  if (z_begin < 0 || z_end > Z || z_begin > z_end || z_begin % N || z_end % N) return HYDRO_EINVAL;
+  if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
+  if (!field_in || !field_out || field_in == field_out) return HYDRO_EINVAL;
+  if (!p->dt_dev && !(p->dt >= 0.0)) return HYDRO_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!finite_pos(p->dx[d])) return HYDRO_EINVAL;
+  long long G = (long long)(X / N) * (Y / N) * ((z_end - z_begin) / N);
+  if (G > 0x7fffffffLL) return HYDRO_EINVAL;
+  WorkTable wt;
+  memset(&wt, 0, sizeof(wt));
+  wt.nseg = 1;
+  wt.total = (int)G;
+  SegDesc& s = wt.seg[0];
+  s.in = field_in;
+  s.out = field_out;
+  s.flux = flux;
+  s.status = dev_status;
+  s.dt_dev = p->dt_dev;
+  s.dt = p->dt;
+  for (int d = 0; d < 3; ++d) s.dx[d] = p->dx[d];
+  s.G = (int)G;
+  s.mode = 1;
+  s.bc = bc;
+  s.X = X;
+  s.Y = Y;
+  s.Z = Z;
+  s.GX = X / N;
+  s.GY = Y / N;
+  s.GZ = (z_end - z_begin) / N;
+  s.gz0 = z_begin / N;
+  s.first = 0;
+  return launch_table(p, wt, N, hydro_required_ghost(p->scheme, p->recon), stream);
+}
+
 int hydro_advance_levels(const hydro_params* p, const hydro_level* levels, int nlev, int N, int ghost, void* stream) {
   if (!p || !valid_enums(p) || !valid_physics(p)) return HYDRO_EINVAL;
   if (nlev < 0 || nlev > HYDRO_MAX_LEVELS || (nlev > 0 && !levels)) return HYDRO_EINVAL;

@@ -121,6 +121,7 @@ def _lib():
         L.hydro_advance.argtypes = [P, vp, vp, vp, i, i, i, vp, vp]
         L.hydro_advance_uniform.argtypes = [P, vp, vp, i, i, i, i, i, vp, vp, vp]
         L.hydro_advance_levels.argtypes = [P, ctypes.POINTER(_CLevel), i, i, i, vp]
+        L.hydro_advance_uniform_zrange.argtypes = [P, vp, vp, i, i, i, i, i, i, i, vp, vp, vp]
         L.hydro_gather_uniform.argtypes = [vp, i, i, i, i, vp, i, i, i, i, vp, vp]
         L.hydro_cfl_workspace_bytes.argtypes = []
         L.hydro_cfl_workspace_bytes.restype = ctypes.c_size_t
@@ -207,6 +208,20 @@ def hydro_advance_uniform(params: Params, field_in, field_out, bc=BC_PERIODIC, f
                                       _ptr(field_out, "field_out", dt), X, Y, Z, N, bc, _ptr(flux, "flux", dt),
                                       _ptr(status, "status", "int32"), _stream(stream))
     _check(rc, "hydro_advance_uniform")
+
+
+def hydro_advance_uniform_zrange(params: Params, field_in, field_out, z_begin, z_end, bc=BC_PERIODIC, flux=None,
+                                 status=None, N=16, stream=None):
+    """hydro_advance_uniform for the groups of the z-slab [z_begin, z_end)
+    only (halos still read from the whole field_in); flux and status keep
+    the whole box's group order."""
+    dt = _storage_dtype(params.precision)
+    _, Z, Y, X = field_in.shape
+    rc = _lib().hydro_advance_uniform_zrange(ctypes.byref(params.c()), _ptr(field_in, "field_in", dt),
+                                             _ptr(field_out, "field_out", dt), X, Y, Z, N, bc, int(z_begin),
+                                             int(z_end), _ptr(flux, "flux", dt), _ptr(status, "status", "int32"),
+                                             _stream(stream))
+    _check(rc, "hydro_advance_uniform_zrange")
 
 
 @dataclass

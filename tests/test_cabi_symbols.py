@@ -23,7 +23,7 @@ def declared():
 
 def test_header_declares_the_boundary():
     names = declared()
-    for n in ("hydro_advance", "hydro_advance_uniform", "hydro_advance_levels", "hydro_gather_uniform",
+    for n in ("hydro_advance", "hydro_advance_uniform", "hydro_advance_uniform_zrange", "hydro_advance_levels", "hydro_gather_uniform",
               "hydro_cfl_dt", "hydro_required_ghost", "hydro_strerror", "hydro_amr_map", "hydro_amr_prepare",
               "hydro_amr_reflux", "hydro_amr_restrict"):
         assert n in names
@@ -42,6 +42,23 @@ def test_library_exports_every_declared_symbol():
     assert lib.hydro_required_ghost(1, 1) == 4 and lib.hydro_required_ghost(5, 0) < 0
     lib.hydro_strerror.restype = ctypes.c_char_p
     assert lib.hydro_strerror(-2).decode().startswith("ghost")
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="no nvcc")
+def test_zrange_arguments_are_checked_on_the_host():
+    """hydro_advance_uniform_zrange rejects a slab that is not a range of
+    whole group layers inside the box before any device work (the pointers
+    are never dereferenced on these paths)."""
+    from paper_1103_3373_gb300 import hydro as H
+    lib = H._lib()
+    p = H.Params(scheme=H.CTU, recon=H.PPM, riemann=H.RS_ROE, precision=H.FP32, dt=0.1, dx=(0.5, 0.5, 0.5)).c()
+    f = lib.hydro_advance_uniform_zrange
+    a, b = ctypes.c_void_p(16), ctypes.c_void_p(32)
+    for z0, z1 in ((8, 32), (0, 40), (32, 16), (-16, 16), (0, 80)):
+        assert f(ctypes.byref(p), a, b, 32, 32, 64, 16, 0, z0, z1, None, None, None) == H.EINVAL, (z0, z1)
+    assert f(ctypes.byref(p), a, b, 32, 32, 64, 8, 0, 0, 16, None, None, None) == H.EUNSUPPORTED
+    assert f(ctypes.byref(p), a, a, 32, 32, 64, 16, 0, 0, 16, None, None, None) == H.EINVAL
 
 
 def test_product_package_does_not_import_the_oracle():

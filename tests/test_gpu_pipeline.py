@@ -1,0 +1,112 @@
+"""GPU tests of the z-slab advance and of the end-to-end stepper that overlaps
+the host transfers with the solver on slabs of patch groups (Sec. 4.1,
+asynchronous memory copy over chunks of patch groups), through the C ABI.
+
+* hydro_advance_uniform_zrange on each slab of a partition of the box: the
+  slab's cells, boundary fluxes and status equal the oracle step of those
+  groups (within the precision's tolerance) and the whole-box advance bit for
+  bit; nothing outside the slab is written; an empty slab is a no-op;
+* the pipelined HostBoxStepper (S slabs; a copy-in, two compute and a
+  copy-out stream) returns the same state and dt as the serial one (copy in,
+  step, copy out) after several steps, for periodic and outflow boxes,
+  unsplit and split schemes.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1103_3373_gb300 import hydro as H
+from paper_1103_3373_gb300 import runtime as RT
+from paper_1103_3373_gb300 import workloads as W
+from tests.gpu_common import TOL_FP32, TOL_FP64, params_pair, quantise, rel_l1, tdtype, with_workspace
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    assert torch.cuda.is_available()
+    return torch, torch.device("cuda:0")
+
+
+def _field(X, Y, Z, seed):
+    c = [W.cell_centres(n)[0] for n in (X, Y, Z)]
+    return W.smooth_field(c[0], c[1], c[2], seed=seed, mach=1.2, modes=8, kmax=4)
+
+
+CASES = [(H.FP64, 0, O.CTU, O.PPM, O.ROE), (H.FP32, 1, O.CTU, O.PPM, O.ROE), (H.FP32_MIXED, 0, O.MHM, O.PPM, O.HLLC),
+         (H.FP32, 0, O.VL, O.PLM, O.HLLE), (H.FP64, 1, O.WAF, O.PLM, O.HLLC), (H.FP32, 0, O.RTVD, O.PLM, O.HLLC)]
+
+
+@pytest.mark.parametrize("prec,bc,scheme,recon,rs", CASES)
+def test_zrange_slabs_equal_whole_box_and_oracle(torch_dev, prec, bc, scheme, recon, rs):
+    torch, dev = torch_dev
+    N = 16
+    X, Y, Z = 32, 32, 80  # 5 group layers: slabs of 1, 3 and 1 layers
+    U = quantise(_field(X, Y, Z, 11), prec)
+    dx = (1.0 / X,) * 3
+    dt = O.cfl_dt(U, dx, 0.4)
+    po, ph = params_pair(scheme, recon, rs, prec, dt, dx, pres_floor=1e-10, dens_floor=1e-10)
+    with_workspace(ph, dev)
+    dtp = tdtype(prec)
+    ft = torch.tensor(U, dtype=dtp, device=dev)
+    G = (X // N) * (Y // N) * (Z // N)
+    whole = torch.empty_like(ft)
+    fl = torch.empty((G, 6, 5, N, N), dtype=dtp, device=dev)
+    st = torch.empty(G, dtype=torch.int32, device=dev)
+    H.hydro_advance_uniform(ph, ft, whole, bc=bc, flux=fl, status=st, N=N)
+    sent = -12345.0
+    part = torch.full_like(ft, sent)
+    fl2 = torch.full_like(fl, sent)
+    st2 = torch.full_like(st, -1)
+    # an empty slab writes nothing
+    H.hydro_advance_uniform_zrange(ph, ft, part, 32, 32, bc=bc, flux=fl2, status=st2, N=N)
+    torch.cuda.synchronize()
+    assert bool((part == sent).all()) and bool((st2 == -1).all())
+    bounds = [0, 16, 64, 80]
+    per_layer = (X // N) * (Y // N)
+    for z0, z1 in zip(bounds[:-1], bounds[1:]):
+        H.hydro_advance_uniform_zrange(ph, ft, part, z0, z1, bc=bc, flux=fl2, status=st2, N=N)
+        torch.cuda.synchronize()
+        got = part.cpu().numpy()
+        # only this slab and the slabs before it are written
+        assert np.all(got[:, z1:] == sent)
+        g1 = z1 // N * per_layer
+        assert bool((st2[g1:] == -1).all()) and bool((fl2[g1:] == sent).all())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(part.cpu().numpy(), whole.cpu().numpy())
+    np.testing.assert_array_equal(fl2.cpu().numpy(), fl.cpu().numpy())
+    np.testing.assert_array_equal(st2.cpu().numpy(), st.cpu().numpy())
+    # and the oracle on the middle slab
+    g = O.required_ghost(scheme, recon)
+    org = W.group_origins(X, Y, Z, N)
+    sel = (org[:, 2] >= 16) & (org[:, 2] < 64)
+    Uo, Fo, So = O.advance(po, O.gather(U, org[sel], N, g, bc=bc), N)
+    got = part.double().cpu().numpy()
+    tol = TOL_FP64 if prec == H.FP64 else TOL_FP32
+    mine = np.stack([got[:, o[2]:o[2] + N, o[1]:o[1] + N, o[0]:o[0] + N] for o in org[sel]])
+    assert rel_l1(mine, Uo) <= tol
+    if prec == H.FP64:
+        np.testing.assert_array_equal(st2.cpu().numpy()[sel], So)
+
+
+@pytest.mark.parametrize("prec,bc,scheme,recon,rs", CASES[:5])
+@pytest.mark.parametrize("slabs", [2, 5])
+def test_pipelined_host_stepper_equals_serial(torch_dev, prec, bc, scheme, recon, rs, slabs):
+    torch, dev = torch_dev
+    X, Y, Z = 32, 32, 80
+    U = _field(X, Y, Z, 12)
+    dx = (1.0 / X,) * 3
+    out = []
+    for S in (1, slabs):
+        _, ph = params_pair(scheme, recon, rs, prec, 0.0, dx, pres_floor=1e-10, dens_floor=1e-10)
+        hs = RT.HostBoxStepper(U, ph, cfl=0.4, bc=bc, device=dev, slabs=S)
+        for _ in range(4):
+            hs.step()
+        torch.cuda.synchronize()
+        out.append((hs.host_in.clone().numpy(), hs.host_dt.clone().numpy(), hs.box.status.cpu().numpy(),
+                    hs.box.flux.cpu().numpy()))
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    assert not np.array_equal(out[0][0], quantise(U, prec).astype(out[0][0].dtype))
