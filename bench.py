@@ -344,6 +344,12 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def slab_arg(s):
+    """'8' -> 8 equal slabs; '1,2,2,1' -> group layers per slab."""
+    parts = [int(x) for x in str(s).split(",") if x.strip()]
+    return parts[0] if len(parts) == 1 else parts
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,9 +358,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mixed / VL detail lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--e2e-slabs", type=int, default=8,
-                    help="z-slabs of the end-to-end pipeline (1: copy in, step, copy out in series)")
-    ap.add_argument("--e2e-sweep", default="", help="also time the end-to-end step at these slab counts (1,2,4,...)")
+    ap.add_argument("--e2e-slabs", default="1,1,2,2,2,2,2,2,1,1",
+                    help="z-slabs of the end-to-end pipeline: a count (1: copy in, step, copy out in series) or "
+                         "group layers per slab, e.g. 1,2,2,2,2,2,2,2,1")
+    ap.add_argument("--e2e-sweep", default="",
+                    help="also time the end-to-end step at these ';'-separated slab settings (e.g. '1;4;8;1,2,2,1')")
     ap.add_argument("--quick", action="store_true", help="main line only (no extra, cpu_baseline or e2e legs)")
     ap.add_argument("--legs", default="all",
                     help="comma list of extra legs to run: precisions, schemes, amr_levels, amr_hierarchy, "
@@ -451,18 +459,20 @@ def main():
             torch.cuda.synchronize()
             e_ms = a.elapsed_time(b)
             out = {"value": world * cells * ke / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": hs.h2d_bytes,
-                   "d2h_bytes_per_step": hs.d2h_bytes, "steps": ke, "ms_per_step": e_ms / ke, "slabs": hs.slabs}
+                   "d2h_bytes_per_step": hs.d2h_bytes, "steps": ke, "ms_per_step": e_ms / ke, "slabs": hs.slabs,
+                   "layers": hs.layers}
             del hs
             return out
-        e2e = e2e_run(args.e2e_slabs)
-        if args.e2e_slabs > 1:
+        e2e = e2e_run(slab_arg(args.e2e_slabs))
+        if e2e["slabs"] > 1:
             s = e2e_run(1)
             e2e["serial"] = {"value": s["value"], "ms_per_step": s["ms_per_step"]}
         if args.e2e_sweep:
             e2e["sweep"] = []
-            for S in (int(x) for x in args.e2e_sweep.split(",")):
-                s = e2e_run(S)
-                e2e["sweep"].append({"slabs": s["slabs"], "value": s["value"], "ms_per_step": s["ms_per_step"]})
+            for S in args.e2e_sweep.split(";"):
+                s = e2e_run(slab_arg(S))
+                e2e["sweep"].append({"slabs": s["slabs"], "layers": s["layers"], "value": s["value"],
+                                     "ms_per_step": s["ms_per_step"]})
 
     extra = {}
     legs = set(args.legs.split(",")) if args.legs != "all" else {"precisions", "schemes", "amr_levels",

@@ -1,0 +1,84 @@
+/*
+ * libhydro — end-to-end step of a uniform box whose state lives in host
+ * memory, with the host<->device copies overlapped with the solver.
+ *
+ * Sec. 4.1 (asynchronous memory copy): the patch groups of one call are split
+ * into chunks and CUDA streams let the copies of one chunk run while the
+ * solver works on another.  Here the chunks are z-slabs of whole group layers
+ * of a uniform field [5][Z][Y][X]:
+ *   - a copy-in stream sends the slabs in an order that completes each slab's
+ *     halo (ghost planes of its neighbours, periodic wrap first);
+ *   - slab s is advanced (hydro_advance_uniform_zrange) as soon as its input
+ *     and halo have arrived, alternately on two compute streams so that the
+ *     last CTAs of one slab overlap the first of the next;
+ *   - a copy-out stream returns slab s while later slabs are advanced;
+ *   - after the last slab, the CFL reduction of the whole new state
+ *     (hydro_cfl_dt) writes the next dt to p->dt_dev, and dt is copied out.
+ * Each copy is one cudaMemcpy2DAsync over the five variables of a z-range.
+ * The result equals hydro_advance_uniform + hydro_cfl_dt on the whole box bit
+ * for bit.
+ *
+ * The pipeline object owns host memory, four CUDA streams and its events (on
+ * the device current at creation); it never allocates device memory and keeps
+ * no caller pointer between calls.
+ */
+#ifndef HYDRO_PIPELINE_H
+#define HYDRO_PIPELINE_H
+
+#include <stddef.h>
+
+#include "hydro.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hydro_pipeline hydro_pipeline;
+
+/*
+ * hydro_pipeline_create — plan the slabs of an X x Y x Z box (multiples of N)
+ * for schemes needing at most `ghost` halo cells (hydro_required_ghost).
+ *   nslab >= 1 slabs; layers = NULL splits the Z/N group layers evenly, else
+ *   layers[s] >= 1 group layers of slab s (sum Z/N).
+ *   bc: HYDRO_BC_PERIODIC or HYDRO_BC_OUTFLOW (fixes the halo order).
+ * Returns HYDRO_EINVAL for bad sizes / layers / ghost >= N,
+ * HYDRO_EUNSUPPORTED for N != 16, HYDRO_ECUDA if streams or events cannot be
+ * created.  *out is set only on HYDRO_OK.
+ */
+int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nslab, const int* layers,
+                          hydro_pipeline** out);
+
+/*
+ * hydro_pipeline_step — one step, enqueued after the work already on
+ * `stream`; the step's completion (state and dt on the host) is ordered
+ * before later work on `stream`.  No host synchronisation.
+ *   p        scheme parameters; p->dt_dev is required (read as this step's dt,
+ *            then overwritten with the next dt); p->workspace serves the
+ *            first compute stream;
+ *   host_in  [5][Z][Y][X] state U^n, page-locked host memory (pageable
+ *            memory works but is not overlapped);
+ *   host_out [5][Z][Y][X] new state, page-locked; may not alias host_in;
+ *   host_dt  optional (NULL): the next dt, page-locked;
+ *   dev_in, dev_out  device fields of the same shape (distinct);
+ *   flux, dev_status optional, as hydro_advance_uniform (whole-box order);
+ *   cfl      Courant number of the next dt;
+ *   red_ws   hydro_cfl_workspace_bytes() of device scratch;
+ *   ws2      the second compute stream's scratch (hydro_workspace_bytes(p);
+ *            may be NULL when that is 0).
+ * Returns HYDRO_EINVAL for bad arguments (also a scheme needing more halo
+ * than the plan's ghost), the codes of hydro_advance_uniform_zrange and
+ * hydro_cfl_dt, or HYDRO_ECUDA.
+ */
+int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* host_in, void* host_out,
+                        double* host_dt, void* dev_in, void* dev_out, void* flux, unsigned* dev_status, double cfl,
+                        void* red_ws, size_t red_ws_bytes, void* ws2, size_t ws2_bytes, void* stream);
+
+/* hydro_pipeline_destroy — release streams, events and the object (NULL: no-op).
+ * Synchronises the pipeline's own streams first. */
+int hydro_pipeline_destroy(hydro_pipeline* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_PIPELINE_H */

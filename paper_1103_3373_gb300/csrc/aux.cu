@@ -74,37 +74,87 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// Pass 1: per CTA and direction d, the maximum over cells of |v_d| + c
-// (c = sqrt(gamma p / rho), primitives with floors), evaluated in the storage
-// precision and kept as FP64; part[d * gridDim.x + b].  Division by dx_d
-// comes once, in pass 2: max_cells((|v_d| + c) / dx_d) equals
-// (max_cells(|v_d| + c)) / dx_d because rounded division by a positive number
-// is monotone.  A NaN cell makes the CTA's partials NaN.
+// Signal speed |v_d| + c of one cell (c = sqrt(gamma p / rho), primitives
+// with floors) folded into the per-direction maxima m[d]; NaN sets bad.
 template <class S>
+__device__ __forceinline__ void fold_speed(const S u[5], const Gas<S>& gas, S m[3], bool& bad) {
+  S w[5];
+  prim<S, false>(u, w, gas);
+  S c = sqrtv(gas.gamma * w[4] / w[0]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    S s = absv(w[1 + d]) + c;
+    if (isnanv(s)) bad = true;
+    m[d] = s > m[d] ? s : m[d];
+  }
+}
+
+template <class S> struct Vec16;
+template <> struct Vec16<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  __device__ __forceinline__ static void split(const V& a, float* o) {
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = a.z;
+    o[3] = a.w;
+  }
+};
+template <> struct Vec16<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  __device__ __forceinline__ static void split(const V& a, double* o) {
+    o[0] = a.x;
+    o[1] = a.y;
+  }
+};
+
+// Pass 1: per CTA and direction d, the maximum over cells of |v_d| + c,
+// evaluated in the storage precision and kept as FP64; part[d * gridDim.x + b].
+// Division by dx_d comes once, in pass 2: max_cells((|v_d| + c) / dx_d) equals
+// (max_cells(|v_d| + c)) / dx_d because rounded division by a positive number
+// is monotone.  A NaN cell makes the CTA's partials NaN.  With VEC, each
+// thread reads 16 bytes per variable (4 FP32 / 2 FP64 cells) per iteration,
+// for more bytes in flight; the caller checks that cells, strides and base
+// are multiples of that width.  The maxima do not depend on the grouping.
+template <class S, bool VEC>
 __global__ void cfl_partial_kernel(const S* __restrict__ U, int G, long long gstride, long long vstride,
                                    long long cells, double gamma, double dfloor, double pfloor,
                                    double* __restrict__ part) {
   __shared__ double sh[32];
   __shared__ int anybad;
   if (threadIdx.x == 0) anybad = 0;
-  const long long total = (long long)G * cells;
   S m[3] = {S(0), S(0), S(0)};
   bool bad = false;
   Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor};
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long gi = e / cells, i = e - gi * cells;
-    const S* b = U + gi * gstride + i;
-    S u[5], w[5];
+  if constexpr (VEC) {
+    using VT = Vec16<S>;
+    constexpr int W = VT::W;
+    const long long cpv = cells / W;
+    const long long total = (long long)G * cpv;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+      long long gi = e / cpv, i = (e - gi * cpv) * W;
+      const S* b = U + gi * gstride + i;
+      S q[5][W];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) u[v] = b[v * vstride];
-    prim<S, false>(u, w, gas);
-    S c = sqrtv(gas.gamma * w[4] / w[0]);
+      for (int v = 0; v < 5; ++v) VT::split(*reinterpret_cast<const typename VT::V*>(b + v * vstride), q[v]);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      S s = absv(w[1 + d]) + c;
-      if (isnanv(s)) bad = true;
-      m[d] = s > m[d] ? s : m[d];
+      for (int k = 0; k < W; ++k) {
+        S u[5] = {q[0][k], q[1][k], q[2][k], q[3][k], q[4][k]};
+        fold_speed(u, gas, m, bad);
+      }
+    }
+  } else {
+    const long long total = (long long)G * cells;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+      long long gi = e / cells, i = e - gi * cells;
+      const S* b = U + gi * gstride + i;
+      S u[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = b[v * vstride];
+      fold_speed(u, gas, m, bad);
     }
   }
   __syncthreads();
@@ -211,10 +261,24 @@ cudaError_t launch_cfl(const void* U, int G, long long gs, long long vs, long lo
   int grid = (int)(want < 4LL * nsm ? want : 4LL * nsm);
   if (grid < 1) grid = 1;
   if (grid > RED_MAX_CTAS) grid = RED_MAX_CTAS;
-  if (dbl)
-    cfl_partial_kernel<double><<<grid, threads, 0, st>>>((const double*)U, G, gs, vs, cells, gamma, dfl, pfl, ws);
-  else
-    cfl_partial_kernel<float><<<grid, threads, 0, st>>>((const float*)U, G, gs, vs, cells, gamma, dfl, pfl, ws);
+  // 16-byte loads when every group's variables start on a 16-byte boundary
+  const int w = dbl ? 2 : 4;
+  const bool vec = ((uintptr_t)U % 16 == 0) && cells % w == 0 && gs % w == 0 && vs % w == 0;
+  if (dbl) {
+    if (vec)
+      cfl_partial_kernel<double, true><<<grid, threads, 0, st>>>((const double*)U, G, gs, vs, cells, gamma, dfl,
+                                                                 pfl, ws);
+    else
+      cfl_partial_kernel<double, false><<<grid, threads, 0, st>>>((const double*)U, G, gs, vs, cells, gamma, dfl,
+                                                                  pfl, ws);
+  } else {
+    if (vec)
+      cfl_partial_kernel<float, true><<<grid, threads, 0, st>>>((const float*)U, G, gs, vs, cells, gamma, dfl, pfl,
+                                                                ws);
+    else
+      cfl_partial_kernel<float, false><<<grid, threads, 0, st>>>((const float*)U, G, gs, vs, cells, gamma, dfl, pfl,
+                                                                 ws);
+  }
   cfl_final_kernel<<<1, 1024, 0, st>>>(ws, grid, dx[0], dx[1], dx[2], cfl, dt, smax);
   return cudaGetLastError();
 }

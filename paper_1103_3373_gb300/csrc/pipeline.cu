@@ -1,0 +1,195 @@
+// End-to-end step of a uniform box with the host<->device copies overlapped
+// with the solver on z-slabs (Sec. 4.1, asynchronous memory copy over chunks
+// of patch groups).  Host-side runtime only: every arithmetic step runs in the
+// group kernels (hydro_advance_uniform_zrange) and the CFL reduction
+// (hydro_cfl_dt).
+#include <cuda_runtime.h>
+
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/hydro.h"
+#include "../../include/hydro_pipeline.h"
+
+namespace hyd {
+int record_cuda_error(cudaError_t e);
+}
+
+struct hydro_pipeline {
+  int X, Y, Z, N, ghost, bc, nslab;
+  std::vector<int> zb;                                  // slab s = planes [zb[s], zb[s+1])
+  std::vector<std::vector<std::pair<int, int>>> chunk;  // input plane ranges completing slab s
+  cudaStream_t s_in = nullptr, s_out = nullptr, s_comp[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_c1 = nullptr, ev_cfl = nullptr, ev_done = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_comp;
+};
+
+namespace {
+
+void release(hydro_pipeline* h) {
+  cudaStream_t ss[4] = {h->s_in, h->s_out, h->s_comp[0], h->s_comp[1]};
+  for (cudaStream_t s : ss)
+    if (s) cudaStreamSynchronize(s);
+  for (cudaEvent_t e : h->ev_in)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_comp)
+    if (e) cudaEventDestroy(e);
+  cudaEvent_t es[4] = {h->ev_start, h->ev_c1, h->ev_cfl, h->ev_done};
+  for (cudaEvent_t e : es)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : ss)
+    if (s) cudaStreamDestroy(s);
+  delete h;
+}
+
+// Input plane ranges per slab, in copy order: the ranges whose arrival
+// completes slab s's input and halo.  Periodic boxes send the last `ghost`
+// planes first (slab 0's lower halo); slab s < S-1 then needs the planes up
+// to zb[s+1] + ghost; the last slab needs the rest.
+void plan(hydro_pipeline* h) {
+  const int S = h->nslab, g = h->ghost, Z = h->Z;
+  const bool periodic = h->bc == HYDRO_BC_PERIODIC;
+  h->chunk.assign(S, {});
+  int lo = 0;
+  for (int s = 0; s < S; ++s) {
+    if (s == 0 && periodic) h->chunk[s].push_back({Z - g, Z});
+    int hi = s < S - 1 ? h->zb[s + 1] + g : (periodic ? Z - g : Z);
+    h->chunk[s].push_back({lo, hi});
+    lo = hi;
+  }
+}
+
+// The five variables of planes [z0, z1) of a [5][Z][Y][X] field, as one 2-D copy.
+cudaError_t copy_planes(void* dst, const void* src, const hydro_pipeline* h, int z0, int z1, size_t es,
+                        cudaMemcpyKind kind, cudaStream_t st) {
+  if (z1 <= z0) return cudaSuccess;
+  const size_t plane = (size_t)h->X * h->Y * es;
+  const size_t pitch = plane * h->Z;
+  const size_t off = plane * z0;
+  return cudaMemcpy2DAsync((char*)dst + off, pitch, (const char*)src + off, pitch, plane * (z1 - z0), 5, kind, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nslab, const int* layers,
+                          hydro_pipeline** out) {
+  if (!out) return HYDRO_EINVAL;
+  if (N != 16) return HYDRO_EUNSUPPORTED;
+  if (X <= 0 || Y <= 0 || Z <= 0 || X % N || Y % N || Z % N) return HYDRO_EINVAL;
+  if (ghost < 0 || ghost >= N) return HYDRO_EINVAL;
+  if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
+  const int GZ = Z / N;
+  if (nslab < 1 || nslab > GZ) return HYDRO_EINVAL;
+  std::vector<int> lay(nslab);
+  if (layers) {
+    int sum = 0;
+    for (int s = 0; s < nslab; ++s) {
+      if (layers[s] < 1) return HYDRO_EINVAL;
+      lay[s] = layers[s];
+      sum += layers[s];
+    }
+    if (sum != GZ) return HYDRO_EINVAL;
+  } else {
+    for (int s = 0; s < nslab; ++s) lay[s] = (s + 1) * GZ / nslab - s * GZ / nslab;
+  }
+  hydro_pipeline* h = new (std::nothrow) hydro_pipeline;
+  if (!h) return HYDRO_EINVAL;
+  h->X = X;
+  h->Y = Y;
+  h->Z = Z;
+  h->N = N;
+  h->ghost = ghost;
+  h->bc = bc;
+  h->nslab = nslab;
+  h->zb.assign(nslab + 1, 0);
+  for (int s = 0; s < nslab; ++s) h->zb[s + 1] = h->zb[s] + lay[s] * N;
+  plan(h);
+  h->ev_in.assign(nslab, nullptr);
+  h->ev_comp.assign(nslab, nullptr);
+  cudaError_t e = cudaSuccess;
+  cudaStream_t* ss[4] = {&h->s_in, &h->s_out, &h->s_comp[0], &h->s_comp[1]};
+  for (cudaStream_t* s : ss)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+  cudaEvent_t* es[4] = {&h->ev_start, &h->ev_c1, &h->ev_cfl, &h->ev_done};
+  for (cudaEvent_t* ev : es)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  for (int s = 0; s < nslab && e == cudaSuccess; ++s) {
+    e = cudaEventCreateWithFlags(&h->ev_in[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[s], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    release(h);
+    return hyd::record_cuda_error(e);
+  }
+  *out = h;
+  return HYDRO_OK;
+}
+
+int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* host_in, void* host_out,
+                        double* host_dt, void* dev_in, void* dev_out, void* flux, unsigned* dev_status, double cfl,
+                        void* red_ws, size_t red_ws_bytes, void* ws2, size_t ws2_bytes, void* stream) {
+  if (!h || !p || !host_in || !host_out || !dev_in || !dev_out || !p->dt_dev) return HYDRO_EINVAL;
+  if (host_in == host_out || dev_in == dev_out || !(cfl > 0.0)) return HYDRO_EINVAL;
+  const int need = hydro_required_ghost(p->scheme, p->recon);
+  if (need < 0 || need > h->ghost) return HYDRO_EINVAL;
+  if (p->precision < HYDRO_FP64 || p->precision > HYDRO_FP32_MIXED) return HYDRO_EINVAL;
+  const size_t es = p->precision == HYDRO_FP64 ? sizeof(double) : sizeof(float);
+  const long long XYZ = (long long)h->X * h->Y * h->Z;
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t* c = h->s_comp;
+  cudaError_t e = cudaEventRecord(h->ev_start, user);
+  cudaStream_t ss[4] = {h->s_in, c[0], c[1], h->s_out};
+  for (cudaStream_t s : ss)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_start, 0);
+  // input, slab by slab
+  for (int s = 0; s < h->nslab && e == cudaSuccess; ++s) {
+    for (const auto& r : h->chunk[s])
+      if (e == cudaSuccess)
+        e = copy_planes(dev_in, host_in, h, r.first, r.second, es, cudaMemcpyHostToDevice, h->s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[s], h->s_in);
+  }
+  if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  // advance each slab when its input is in; return it at once
+  hydro_params p2 = *p;
+  p2.workspace = ws2;
+  p2.workspace_bytes = ws2_bytes;
+  const hydro_params* pc[2] = {p, &p2};
+  for (int s = 0; s < h->nslab; ++s) {
+    const int k = s & 1;
+    e = cudaStreamWaitEvent(c[k], h->ev_in[s], 0);
+    if (e != cudaSuccess) return hyd::record_cuda_error(e);
+    int rc = hydro_advance_uniform_zrange(pc[k], dev_in, dev_out, h->X, h->Y, h->Z, h->N, h->bc, h->zb[s],
+                                          h->zb[s + 1], flux, dev_status, c[k]);
+    if (rc != HYDRO_OK) return rc;
+    e = cudaEventRecord(h->ev_comp[s], c[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_comp[s], 0);
+    if (e == cudaSuccess)
+      e = copy_planes(host_out, dev_out, h, h->zb[s], h->zb[s + 1], es, cudaMemcpyDeviceToHost, h->s_out);
+    if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  }
+  // next dt from the whole new state, after both compute streams
+  e = cudaEventRecord(h->ev_c1, c[1]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c[0], h->ev_c1, 0);
+  if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  int rc = hydro_cfl_dt(dev_out, 1, 5 * XYZ, XYZ, XYZ, p->precision, p->gamma, p->dens_floor, p->pres_floor, p->dx,
+                        cfl, const_cast<double*>(p->dt_dev), nullptr, red_ws, red_ws_bytes, c[0]);
+  if (rc != HYDRO_OK) return rc;
+  e = cudaEventRecord(h->ev_cfl, c[0]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_cfl, 0);
+  if (e == cudaSuccess && host_dt)
+    e = cudaMemcpyAsync(host_dt, p->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s_out);
+  // the caller's stream resumes after the copies out (which follow everything)
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_done, h->s_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->ev_done, 0);
+  return e == cudaSuccess ? HYDRO_OK : hyd::record_cuda_error(e);
+}
+
+int hydro_pipeline_destroy(hydro_pipeline* h) {
+  if (h) release(h);
+  return HYDRO_OK;
+}
+
+}  // extern "C"

@@ -122,6 +122,10 @@ def _lib():
         L.hydro_advance_uniform.argtypes = [P, vp, vp, i, i, i, i, i, vp, vp, vp]
         L.hydro_advance_levels.argtypes = [P, ctypes.POINTER(_CLevel), i, i, i, vp]
         L.hydro_advance_uniform_zrange.argtypes = [P, vp, vp, i, i, i, i, i, i, i, vp, vp, vp]
+        L.hydro_pipeline_create.argtypes = [i, i, i, i, i, i, i, vp, ctypes.POINTER(vp)]
+        L.hydro_pipeline_step.argtypes = [vp, P, vp, vp, vp, vp, vp, vp, vp, d, vp, ctypes.c_size_t, vp,
+                                          ctypes.c_size_t, vp]
+        L.hydro_pipeline_destroy.argtypes = [vp]
         L.hydro_gather_uniform.argtypes = [vp, i, i, i, i, vp, i, i, i, i, vp, vp]
         L.hydro_cfl_workspace_bytes.argtypes = []
         L.hydro_cfl_workspace_bytes.restype = ctypes.c_size_t
@@ -222,6 +226,57 @@ def hydro_advance_uniform_zrange(params: Params, field_in, field_out, z_begin, z
                                              int(z_end), _ptr(flux, "flux", dt), _ptr(status, "status", "int32"),
                                              _stream(stream))
     _check(rc, "hydro_advance_uniform_zrange")
+
+
+def _host_ptr(t, name, dtype=None):
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous host tensor" % name)
+    if dtype is not None and str(t.dtype).split(".")[-1] != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    return t.data_ptr()
+
+
+class Pipeline:
+    """hydro_pipeline (include/hydro_pipeline.h): the end-to-end step of a
+    uniform box held in page-locked host memory, copies overlapped with the
+    solver on z-slabs (Sec. 4.1).  slabs: a count (even split of the group
+    layers) or a list of group layers per slab."""
+
+    def __init__(self, X, Y, Z, ghost, bc=BC_PERIODIC, slabs=8, N=16):
+        if isinstance(slabs, (list, tuple)):
+            n, lay = len(slabs), (ctypes.c_int * len(slabs))(*[int(a) for a in slabs])
+        else:
+            n, lay = int(slabs), None
+        h = ctypes.c_void_p()
+        _check(_lib().hydro_pipeline_create(X, Y, Z, N, ghost, bc, n, lay, ctypes.byref(h)), "hydro_pipeline_create")
+        self._h = h
+        self.shape = (5, Z, Y, X)
+        self.nslab = n
+
+    def step(self, params: Params, host_in, host_out, dev_in, dev_out, cfl, red_ws, host_dt=None, flux=None,
+             status=None, ws2=None, stream=None):
+        dt = _storage_dtype(params.precision)
+        for a in (host_in, host_out, dev_in, dev_out):
+            if tuple(a.shape) != self.shape:
+                raise ValueError("field shape %s, pipeline planned for %s" % (tuple(a.shape), self.shape))
+        rc = _lib().hydro_pipeline_step(self._h, ctypes.byref(params.c()), _host_ptr(host_in, "host_in", dt),
+                                        _host_ptr(host_out, "host_out", dt), _host_ptr(host_dt, "host_dt", "float64"),
+                                        _ptr(dev_in, "dev_in", dt), _ptr(dev_out, "dev_out", dt),
+                                        _ptr(flux, "flux", dt), _ptr(status, "status", "int32"), float(cfl),
+                                        red_ws.data_ptr(), red_ws.numel() * red_ws.element_size(),
+                                        ws2.data_ptr() if ws2 is not None else None,
+                                        ws2.numel() * ws2.element_size() if ws2 is not None else 0, _stream(stream))
+        _check(rc, "hydro_pipeline_step")
+
+    def close(self):
+        if getattr(self, "_h", None) and _LIB is not None:
+            _LIB.hydro_pipeline_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 @dataclass

@@ -5,8 +5,6 @@ of a step, and helpers shared by the batched / serving forms.
 Every numerical step runs in libhydro's kernels; this module only owns device
 buffers (through PyTorch) and orders the calls on a stream.
 """
-import copy
-
 import numpy as np
 
 from . import hydro as H
@@ -97,117 +95,48 @@ class HostBoxStepper:
     """End-to-end form of UniformBox.step for a caller that keeps its data on
     the host: each step copies the state in from pinned host memory, runs the
     step on the device and copies the new state and dt back (the paper times
-    its GPU solver the same way, Sec. 3.2).
+    its GPU solver the same way, Sec. 3.2).  The step is one native call
+    (hydro_pipeline_step).
 
     slabs = 1: copy in, advance, copy out, one after the other.
-    slabs = S > 1: the asynchronous-copy scheme of Sec. 4.1 on z-slabs of
-    group layers.  The input arrives on one copy stream in chunks ordered so
-    that the chunk ending g planes past slab s completes the halo of slab s
-    (the last g planes of the box, needed by slab 0 of a periodic box, come
-    first); slab s is advanced (hydro_advance_uniform_zrange) as soon as its
-    chunk is in, while the next chunk is still copying; its new state is
-    copied out on a second copy stream while the next slab is advanced.  The
-    slabs alternate between two compute streams, so the last CTAs of one slab
-    overlap the first of the next (a slab holds few groups per CTA; each
-    stream has its own scratch workspace).  The CFL reduction of the whole
-    new state follows the last slab.  Every copy is one contiguous range of
-    one variable.  The result equals slabs = 1 bit for bit (the groups of a
-    slab compute exactly what they compute in the whole box).
+    slabs = S > 1 (S equal slabs) or a list of group-layer counts per slab:
+    the asynchronous-copy scheme of Sec. 4.1 on z-slabs of group layers (a
+    copy-in stream, two compute streams alternating slabs, a copy-out stream;
+    see include/hydro_pipeline.h).  The result equals UniformBox.step bit for
+    bit.
     """
 
     def __init__(self, U0, params: H.Params, cfl=0.4, bc=H.BC_PERIODIC, N=16, device="cuda:0", slabs=1):
         torch = _torch()
         self.torch = torch
         self.box = UniformBox(U0, params, cfl=cfl, bc=bc, N=N, device=device)
-        self.host_in = torch.empty(self.box.shape, dtype=self.box.dtype).pin_memory()
-        self.host_in.copy_(torch.as_tensor(U0, dtype=self.box.dtype))
+        b = self.box
+        self.host_in = torch.empty(b.shape, dtype=b.dtype).pin_memory()
+        self.host_in.copy_(torch.as_tensor(U0, dtype=b.dtype))
         self.host_out = torch.empty_like(self.host_in).pin_memory()
         self.host_dt = torch.zeros(1, dtype=torch.float64).pin_memory()
         self.h2d_bytes = self.host_in.numel() * self.host_in.element_size()
         self.d2h_bytes = self.h2d_bytes + 8
-        Z = self.box.shape[1]
+        _, Z, Y, X = b.shape
         GZ = Z // N
-        self.slabs = max(1, min(int(slabs), GZ))
-        if self.slabs > 1:
-            S = self.slabs
-            self.zb = [(s * GZ // S) * N for s in range(S + 1)]
-            self.chunks = self._chunks(Z, H.hydro_required_ghost(params.scheme, params.recon), bc)
-            dev = self.box.dev
-            self.s_in = torch.cuda.Stream(device=dev)
-            self.s_comp = [torch.cuda.Stream(device=dev) for _ in range(2)]
-            self.s_out = torch.cuda.Stream(device=dev)
-            self.ev_in = [torch.cuda.Event() for _ in range(S)]
-            self.ev_comp = [torch.cuda.Event() for _ in range(S + 1)]
-            # the second compute stream's own copy of the parameters (the
-            # device dt is shared; the scratch workspace is not)
-            p2 = copy.copy(self.box.p)
-            nws = H.hydro_workspace_bytes(p2, N)
-            p2.workspace = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None
-            self.p_comp = [self.box.p, p2]
-
-    def _chunks(self, Z, g, bc):
-        """Input plane ranges per slab: chunks[s] = the ranges whose arrival
-        completes slab s's input, halo included (copied in this order)."""
-        S, zb = self.slabs, self.zb
-        out = []
-        lo = 0
-        for s in range(S):
-            rng = []
-            if s == 0 and bc == H.BC_PERIODIC:
-                rng.append((Z - g, Z))
-            hi = zb[s + 1] + g if s < S - 1 else (Z - g if bc == H.BC_PERIODIC else Z)
-            rng.append((lo, hi))
-            lo = hi
-            out.append(rng)
-        return out
+        if not isinstance(slabs, (list, tuple)):
+            slabs = max(1, min(int(slabs), GZ))
+        ghost = H.hydro_required_ghost(params.scheme, params.recon)
+        with torch.cuda.device(b.dev):
+            self.pipe = H.Pipeline(X, Y, Z, ghost, bc=bc, slabs=slabs, N=N)
+        self.slabs = self.pipe.nslab
+        self.layers = list(slabs) if isinstance(slabs, (list, tuple)) else \
+            [(s + 1) * GZ // slabs - s * GZ // slabs for s in range(slabs)]
+        nws = H.hydro_workspace_bytes(b.p, N)
+        self.ws2 = torch.empty(nws, dtype=torch.uint8, device=b.dev) if nws else None
 
     def step(self):
-        if self.slabs > 1:
-            return self._step_pipelined()
         b = self.box
-        b.a.copy_(self.host_in, non_blocking=True)
-        b.step()
-        self.host_out.copy_(b.a, non_blocking=True)
-        self.host_dt.copy_(b.dt, non_blocking=True)
-        # the next step starts from the state just returned
-        self.host_in, self.host_out = self.host_out, self.host_in
-
-    def _step_pipelined(self):
-        torch = self.torch
-        b = self.box
-        cur = torch.cuda.current_stream(b.dev)
-        sc = self.s_comp
-        # the previous step (its copies out included) precedes this one
-        for s in (self.s_in, sc[0], sc[1], self.s_out):
-            s.wait_stream(cur)
-        with torch.cuda.stream(self.s_in):
-            for s, rng in enumerate(self.chunks):
-                for z0, z1 in rng:
-                    for v in range(5):
-                        b.a[v, z0:z1].copy_(self.host_in[v, z0:z1], non_blocking=True)
-                self.ev_in[s].record(self.s_in)
-        self.p_comp[1].split_order = b.p.split_order
-        for s in range(self.slabs):
-            c = sc[s & 1]
-            c.wait_event(self.ev_in[s])
-            H.hydro_advance_uniform_zrange(self.p_comp[s & 1], b.a, b.b, self.zb[s], self.zb[s + 1], bc=b.bc,
-                                           flux=b.flux, status=b.status, N=b.N, stream=c)
-            self.ev_comp[s].record(c)
-            self.s_out.wait_event(self.ev_comp[s])
-            with torch.cuda.stream(self.s_out):
-                z0, z1 = self.zb[s], self.zb[s + 1]
-                for v in range(5):
-                    self.host_out[v, z0:z1].copy_(b.b[v, z0:z1], non_blocking=True)
+        self.pipe.step(b.p, self.host_in, self.host_out, b.a, b.b, b.cfl, b.red_ws, host_dt=self.host_dt,
+                       flux=b.flux, status=b.status, ws2=self.ws2, stream=b.stream)
         b.swap()
-        sc[0].wait_stream(sc[1])
-        b.compute_dt(stream=sc[0])
-        self.ev_comp[self.slabs].record(sc[0])
-        self.s_out.wait_event(self.ev_comp[self.slabs])
-        with torch.cuda.stream(self.s_out):
-            self.host_dt.copy_(b.dt, non_blocking=True)
-        cur.wait_stream(self.s_out)
-        cur.wait_stream(sc[0])
         b.end_step()
+        # the next step starts from the state just returned
         self.host_in, self.host_out = self.host_out, self.host_in
 
 

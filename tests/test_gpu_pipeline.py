@@ -6,10 +6,11 @@ asynchronous memory copy over chunks of patch groups), through the C ABI.
   slab's cells, boundary fluxes and status equal the oracle step of those
   groups (within the precision's tolerance) and the whole-box advance bit for
   bit; nothing outside the slab is written; an empty slab is a no-op;
-* the pipelined HostBoxStepper (S slabs; a copy-in, two compute and a
-  copy-out stream) returns the same state and dt as the serial one (copy in,
-  step, copy out) after several steps, for periodic and outflow boxes,
-  unsplit and split schemes.
+* the end-to-end HostBoxStepper (hydro_pipeline_step: 1 slab, or S slabs on
+  a copy-in, two compute and a copy-out stream) returns the state, dt,
+  boundary fluxes and status of the same number of device-resident steps,
+  for periodic and outflow boxes, unsplit and split schemes; bad plans and
+  a scheme needing more halo than planned are rejected.
 """
 import numpy as np
 import pytest
@@ -92,21 +93,47 @@ def test_zrange_slabs_equal_whole_box_and_oracle(torch_dev, prec, bc, scheme, re
 
 
 @pytest.mark.parametrize("prec,bc,scheme,recon,rs", CASES[:5])
-@pytest.mark.parametrize("slabs", [2, 5])
-def test_pipelined_host_stepper_equals_serial(torch_dev, prec, bc, scheme, recon, rs, slabs):
+@pytest.mark.parametrize("slabs", [1, 2, 5, (1, 3, 1)])
+def test_host_stepper_equals_device_steps(torch_dev, prec, bc, scheme, recon, rs, slabs):
+    """Four end-to-end steps through hydro_pipeline_step (host buffers in and
+    out) give the bytes of four device-resident UniformBox steps: state, dt,
+    boundary fluxes and status."""
     torch, dev = torch_dev
     X, Y, Z = 32, 32, 80
     U = _field(X, Y, Z, 12)
     dx = (1.0 / X,) * 3
-    out = []
-    for S in (1, slabs):
-        _, ph = params_pair(scheme, recon, rs, prec, 0.0, dx, pres_floor=1e-10, dens_floor=1e-10)
-        hs = RT.HostBoxStepper(U, ph, cfl=0.4, bc=bc, device=dev, slabs=S)
-        for _ in range(4):
-            hs.step()
-        torch.cuda.synchronize()
-        out.append((hs.host_in.clone().numpy(), hs.host_dt.clone().numpy(), hs.box.status.cpu().numpy(),
-                    hs.box.flux.cpu().numpy()))
-    for a, b in zip(out[0], out[1]):
-        np.testing.assert_array_equal(a, b)
-    assert not np.array_equal(out[0][0], quantise(U, prec).astype(out[0][0].dtype))
+
+    def params():
+        return params_pair(scheme, recon, rs, prec, 0.0, dx, pres_floor=1e-10, dens_floor=1e-10)[1]
+
+    box = RT.UniformBox(U, params(), cfl=0.4, bc=bc, device=dev)
+    hs = RT.HostBoxStepper(U, params(), cfl=0.4, bc=bc, device=dev, slabs=slabs)
+    assert hs.slabs == (len(slabs) if isinstance(slabs, tuple) else slabs)
+    for _ in range(4):
+        box.step()
+        hs.step()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hs.host_in.numpy(), box.state().cpu().numpy())
+    np.testing.assert_array_equal(hs.host_dt.numpy(), box.dt.cpu().numpy())
+    np.testing.assert_array_equal(hs.box.status.cpu().numpy(), box.status.cpu().numpy())
+    np.testing.assert_array_equal(hs.box.flux.cpu().numpy(), box.flux.cpu().numpy())
+    assert not np.array_equal(hs.host_in.numpy(), quantise(U, prec).astype(hs.host_in.numpy().dtype))
+
+
+def test_pipeline_argument_errors(torch_dev):
+    torch, dev = torch_dev
+    with pytest.raises(H.HydroError):
+        H.Pipeline(32, 32, 80, 3, slabs=(2, 2))          # layers do not sum to Z/N
+    with pytest.raises(H.HydroError):
+        H.Pipeline(32, 32, 80, 3, slabs=6)               # more slabs than group layers
+    pipe = H.Pipeline(32, 32, 64, 2, slabs=2)
+    p = H.Params(scheme=H.CTU, recon=H.PPM, riemann=H.RS_ROE, precision=H.FP32, dx=(0.1,) * 3,
+                 dt_dev=torch.zeros(1, dtype=torch.float64, device=dev))
+    a = torch.zeros((5, 64, 32, 32), dtype=torch.float32).pin_memory()
+    b = torch.zeros_like(a).pin_memory()
+    da = torch.zeros((5, 64, 32, 32), dtype=torch.float32, device=dev)
+    db = torch.zeros_like(da)
+    ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    with pytest.raises(H.HydroError):                    # PPM + CTU needs 3 ghost layers, planned for 2
+        pipe.step(p, a, b, da, db, 0.4, ws)
+    pipe.close()
