@@ -13,14 +13,18 @@
  *     last CTAs of one slab overlap the first of the next;
  *   - a copy-out stream returns slab s while later slabs are advanced;
  *   - after the last slab, the CFL reduction of the whole new state
- *     (hydro_cfl_dt) writes the next dt to p->dt_dev, and dt is copied out.
+ *     (hydro_cfl_dt) writes the next dt to p->dt_dev, and dt is copied out;
+ *   - consecutive steps on rotating buffers overlap: the next step's
+ *     copy-in of a slab starts once this step has returned the slabs it
+ *     covers (see hydro_pipeline_step).
  * Each copy is one cudaMemcpy2DAsync over the five variables of a z-range.
  * The result equals hydro_advance_uniform + hydro_cfl_dt on the whole box bit
  * for bit.
  *
  * The pipeline object owns host memory, four CUDA streams and its events (on
- * the device current at creation); it never allocates device memory and keeps
- * no caller pointer between calls.
+ * the device current at creation); it never allocates device memory.  Between
+ * calls it keeps the last step's buffer addresses, only to recognise a
+ * chained step; it never reads through them.
  */
 #ifndef HYDRO_PIPELINE_H
 #define HYDRO_PIPELINE_H
@@ -49,9 +53,17 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
                           hydro_pipeline** out);
 
 /*
- * hydro_pipeline_step — one step, enqueued after the work already on
- * `stream`; the step's completion (state and dt on the host) is ordered
- * before later work on `stream`.  No host synchronisation.
+ * hydro_pipeline_step — one step; its completion (state and dt on the host)
+ * is ordered before later work on `stream`.  No host synchronisation.
+ *   Chained steps: when host_in is the last step's host_out, dev_in is
+ *   neither of the last step's device buffers and dev_out is not the last
+ *   step's dev_out (three device buffers in rotation: in = D[2n % 3],
+ *   out = D[(2n+1) % 3]), the step is ordered after the last step only:
+ *   each input chunk waits for the last step's copy-out of the slabs it
+ *   covers, and the advances wait for the last step's dt.  Its copy-in thus
+ *   overlaps the end of the last step.  Work the caller put on `stream`
+ *   after the last step is then not waited for.  Any other step (the first
+ *   one, or other buffers) starts after the work already on `stream`.
  *   p        scheme parameters; p->dt_dev is required (read as this step's dt,
  *            then overwritten with the next dt); p->workspace serves the
  *            first compute stream;

@@ -23,6 +23,12 @@ struct hydro_pipeline {
   cudaStream_t s_in = nullptr, s_out = nullptr, s_comp[2] = {nullptr, nullptr};
   cudaEvent_t ev_start = nullptr, ev_c1 = nullptr, ev_cfl = nullptr, ev_done = nullptr;
   std::vector<cudaEvent_t> ev_in, ev_comp;
+  std::vector<cudaEvent_t> ev_out;  // copy-out of slab s done (last step)
+  // buffers of the last step (chained steps: see hydro_pipeline_step)
+  bool has_prev = false;
+  const void* prev_host_out = nullptr;
+  const void* prev_dev_in = nullptr;
+  const void* prev_dev_out = nullptr;
 };
 
 namespace {
@@ -34,6 +40,8 @@ void release(hydro_pipeline* h) {
   for (cudaEvent_t e : h->ev_in)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_comp)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_out)
     if (e) cudaEventDestroy(e);
   cudaEvent_t es[4] = {h->ev_start, h->ev_c1, h->ev_cfl, h->ev_done};
   for (cudaEvent_t e : es)
@@ -109,6 +117,7 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
   plan(h);
   h->ev_in.assign(nslab, nullptr);
   h->ev_comp.assign(nslab, nullptr);
+  h->ev_out.assign(nslab, nullptr);
   cudaError_t e = cudaSuccess;
   cudaStream_t* ss[4] = {&h->s_in, &h->s_out, &h->s_comp[0], &h->s_comp[1]};
   for (cudaStream_t* s : ss)
@@ -119,6 +128,7 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
   for (int s = 0; s < nslab && e == cudaSuccess; ++s) {
     e = cudaEventCreateWithFlags(&h->ev_in[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[s], cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     release(h);
@@ -140,15 +150,32 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   const long long XYZ = (long long)h->X * h->Y * h->Z;
   cudaStream_t user = (cudaStream_t)stream;
   cudaStream_t* c = h->s_comp;
-  cudaError_t e = cudaEventRecord(h->ev_start, user);
-  cudaStream_t ss[4] = {h->s_in, c[0], c[1], h->s_out};
-  for (cudaStream_t s : ss)
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_start, 0);
+  // Chained step: the input is the last step's output on the host and the
+  // device input buffer is neither of the last step's.  Then each input
+  // chunk only waits for the last step's copies out of the slabs it covers,
+  // and the slab advances wait for the last step's dt (which follows all of
+  // its advances): the copy-in overlaps the end of the last step.
+  const bool chained = h->has_prev && host_in == h->prev_host_out && dev_in != h->prev_dev_in &&
+                       dev_in != h->prev_dev_out && dev_out != h->prev_dev_out;
+  cudaError_t e = cudaSuccess;
+  if (chained) {
+    e = cudaStreamWaitEvent(c[0], h->ev_cfl, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c[1], h->ev_cfl, 0);
+  } else {
+    e = cudaEventRecord(h->ev_start, user);
+    cudaStream_t ss[4] = {h->s_in, c[0], c[1], h->s_out};
+    for (cudaStream_t s : ss)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_start, 0);
+  }
   // input, slab by slab
   for (int s = 0; s < h->nslab && e == cudaSuccess; ++s) {
-    for (const auto& r : h->chunk[s])
+    for (const auto& r : h->chunk[s]) {
+      if (chained)
+        for (int t = 0; t < h->nslab && e == cudaSuccess; ++t)
+          if (h->zb[t] < r.second && r.first < h->zb[t + 1]) e = cudaStreamWaitEvent(h->s_in, h->ev_out[t], 0);
       if (e == cudaSuccess)
         e = copy_planes(dev_in, host_in, h, r.first, r.second, es, cudaMemcpyHostToDevice, h->s_in);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[s], h->s_in);
   }
   if (e != cudaSuccess) return hyd::record_cuda_error(e);
@@ -168,6 +195,7 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_comp[s], 0);
     if (e == cudaSuccess)
       e = copy_planes(host_out, dev_out, h, h->zb[s], h->zb[s + 1], es, cudaMemcpyDeviceToHost, h->s_out);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[s], h->s_out);
     if (e != cudaSuccess) return hyd::record_cuda_error(e);
   }
   // next dt from the whole new state, after both compute streams
@@ -177,14 +205,20 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   int rc = hydro_cfl_dt(dev_out, 1, 5 * XYZ, XYZ, XYZ, p->precision, p->gamma, p->dens_floor, p->pres_floor, p->dx,
                         cfl, const_cast<double*>(p->dt_dev), nullptr, red_ws, red_ws_bytes, c[0]);
   if (rc != HYDRO_OK) return rc;
-  e = cudaEventRecord(h->ev_cfl, c[0]);
+  // dt to the host on the same stream, before the next step's reduction can
+  // overwrite it (the next step's advances wait for ev_cfl)
+  if (host_dt) e = cudaMemcpyAsync(host_dt, p->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, c[0]);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_cfl, c[0]);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_cfl, 0);
-  if (e == cudaSuccess && host_dt)
-    e = cudaMemcpyAsync(host_dt, p->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s_out);
   // the caller's stream resumes after the copies out (which follow everything)
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_done, h->s_out);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->ev_done, 0);
-  return e == cudaSuccess ? HYDRO_OK : hyd::record_cuda_error(e);
+  if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  h->has_prev = true;
+  h->prev_host_out = host_out;
+  h->prev_dev_in = dev_in;
+  h->prev_dev_out = dev_out;
+  return HYDRO_OK;
 }
 
 int hydro_pipeline_destroy(hydro_pipeline* h) {

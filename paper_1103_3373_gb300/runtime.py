@@ -102,8 +102,9 @@ class HostBoxStepper:
     slabs = S > 1 (S equal slabs) or a list of group-layer counts per slab:
     the asynchronous-copy scheme of Sec. 4.1 on z-slabs of group layers (a
     copy-in stream, two compute streams alternating slabs, a copy-out stream;
-    see include/hydro_pipeline.h).  The result equals UniformBox.step bit for
-    bit.
+    see include/hydro_pipeline.h); consecutive steps overlap (the copy-in of
+    one starts while the last finishes) on three device fields in rotation.
+    The result equals UniformBox.step bit for bit.
     """
 
     def __init__(self, U0, params: H.Params, cfl=0.4, bc=H.BC_PERIODIC, N=16, device="cuda:0", slabs=1):
@@ -129,12 +130,20 @@ class HostBoxStepper:
             [(s + 1) * GZ // slabs - s * GZ // slabs for s in range(slabs)]
         nws = H.hydro_workspace_bytes(b.p, N)
         self.ws2 = torch.empty(nws, dtype=torch.uint8, device=b.dev) if nws else None
+        # three device fields in rotation (in = D[2n % 3], out = D[(2n+1) % 3]):
+        # consecutive steps then chain, the copy-in of one overlapping the
+        # end of the last (include/hydro_pipeline.h)
+        self.dev_fields = [b.a, b.b, torch.empty_like(b.a)]
+        self.n = 0
 
     def step(self):
         b = self.box
-        self.pipe.step(b.p, self.host_in, self.host_out, b.a, b.b, b.cfl, b.red_ws, host_dt=self.host_dt,
+        d = self.dev_fields
+        din, dout = d[(2 * self.n) % 3], d[(2 * self.n + 1) % 3]
+        self.pipe.step(b.p, self.host_in, self.host_out, din, dout, b.cfl, b.red_ws, host_dt=self.host_dt,
                        flux=b.flux, status=b.status, ws2=self.ws2, stream=b.stream)
-        b.swap()
+        b.a, b.b = dout, din
+        self.n += 1
         b.end_step()
         # the next step starts from the state just returned
         self.host_in, self.host_out = self.host_out, self.host_in

@@ -120,6 +120,33 @@ def test_host_stepper_equals_device_steps(torch_dev, prec, bc, scheme, recon, rs
     assert not np.array_equal(hs.host_in.numpy(), quantise(U, prec).astype(hs.host_in.numpy().dtype))
 
 
+@pytest.mark.parametrize("slabs", [1, 3])
+def test_unchained_steps_equal_device_steps(torch_dev, slabs):
+    """Two device buffers in ping-pong (the next step's input is the last
+    step's output buffer): every step then waits for the work on the stream
+    instead of chaining, and the result is the same."""
+    torch, dev = torch_dev
+    X, Y, Z = 32, 32, 48
+    U = _field(X, Y, Z, 13)
+    dx = (1.0 / X,) * 3
+    _, p1 = params_pair(O.CTU, O.PPM, O.ROE, H.FP32, 0.0, dx)
+    _, p2 = params_pair(O.CTU, O.PPM, O.ROE, H.FP32, 0.0, dx)
+    box = RT.UniformBox(U, p1, cfl=0.4, device=dev)
+    ref = RT.UniformBox(U, p2, cfl=0.4, device=dev)
+    pipe = H.Pipeline(X, Y, Z, 3, slabs=slabs)
+    hin = torch.tensor(U, dtype=torch.float32).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(3):
+        pipe.step(box.p, hin, hout, box.a, box.b, 0.4, box.red_ws, flux=box.flux, status=box.status)
+        box.swap()
+        hin, hout = hout, hin
+        ref.step()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hin.numpy(), ref.state().cpu().numpy())
+    np.testing.assert_array_equal(box.dt.cpu().numpy(), ref.dt.cpu().numpy())
+    pipe.close()
+
+
 def test_pipeline_argument_errors(torch_dev):
     torch, dev = torch_dev
     with pytest.raises(H.HydroError):
