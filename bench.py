@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s (CTU+PPM+Roe, FP32 vs FP64) and % roofline; p50/p99 step latency"
 UNIT = "cell-updates/s"
 N_BOX = 256
+FP64_NOMINAL_TFLOPS = 1.25  # the part's FP64 rate (not a measured peak)
 CFL = 0.4
 FLOORS = dict(dens_floor=1e-6, pres_floor=1e-6)
 CONFIG = {"workload": "uniform 256^3 periodic box as 4096 16^3-cell patch groups (3 ghost layers); lognormal "
@@ -368,7 +369,7 @@ def main():
                     help="comma list of extra legs to run: precisions, schemes, amr_levels, amr_hierarchy, "
                          "serving (default all)")
     ap.add_argument("--block-threads", type=int, default=0,
-                    help="use this many threads per CTA for the main line instead of autotuning")
+                    help="use this many threads per CTA (capped per kernel) instead of autotuning")
     args = ap.parse_args()
     if args.quick:
         args.no_extra = args.no_cpu = True
@@ -480,6 +481,15 @@ def main():
     if not args.no_extra and rank == 0:
         del box
         torch.cuda.empty_cache()
+        with open(os.path.join(ROOT, "paper_1103_3373_gb300", "data", "flops_per_cell.json")) as fh:
+            flops_tab = json.load(fh)["entries"]
+
+        def leg_roofline(key, kernel_ms, pk, note):
+            a = flops_tab[key]["flops"] * cells / (kernel_ms / 1e3) / 1e12
+            return {"flops_per_cell": flops_tab[key]["flops"], "achieved_tflops": a, "peak_tflops": pk,
+                    "frac": a / pk, "peak_note": note}
+
+        fp32_note = "derived FP32 ALU peak (as the main line)"
         for name, prec, k in (("fp64", H.FP64, 4), ("mixed", H.FP32_MIXED, 50)) if "precisions" in legs else ():
             bx = RT.UniformBox(U, make_params(H, prec, dx), cfl=CFL, device=dev, stream=stream)
             tb = bx.tune() if prec != H.FP64 else None
@@ -487,22 +497,33 @@ def main():
             sm, am, tm, _ = time_box(bx, k, 3, torch)
             extra[name] = {"value": cells * k / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / k,
                            "kernel_ms": am, "steps": k,
-                           "block_threads": tb["block_threads"] if tb else bx.p.block_threads}
+                           "block_threads": tb["block_threads"] if tb else bx.p.block_threads,
+                           "roofline": leg_roofline("ctu-ppm-roe", am, FP64_NOMINAL_TFLOPS if prec == H.FP64 else peak,
+                                                    "nominal FP64 rate of the part, not measured" if prec == H.FP64
+                                                    else fp32_note)}
             del bx
             torch.cuda.empty_cache()
-        for tag, sch, rec, rs, ch in (("vl_plm_hllc_fp32", H.VL, H.PLM, H.RS_HLLC, 0),
-                                      ("mhm_ppm_roe_fp32", H.MHM, H.PPM, H.RS_ROE, 0),
-                                      ("ctu_ppm_roe_characteristic_fp32", H.CTU, H.PPM, H.RS_ROE, 1),
-                                      ("rtvd_fp32", H.RTVD, H.PLM, H.RS_HLLC, 0),
-                                      ("waf_hllc_fp32", H.WAF, H.PLM, H.RS_HLLC, 0)) if "schemes" in legs else ():
+        for tag, sch, rec, rs, ch, fkey in (("vl_plm_hllc_fp32", H.VL, H.PLM, H.RS_HLLC, 0, "vl-plm-hllc"),
+                                            ("mhm_ppm_roe_fp32", H.MHM, H.PPM, H.RS_ROE, 0, "mhm-ppm-roe"),
+                                            ("ctu_ppm_roe_characteristic_fp32", H.CTU, H.PPM, H.RS_ROE, 1,
+                                             "ctu-ppm-roe-char"),
+                                            ("rtvd_fp32", H.RTVD, H.PLM, H.RS_HLLC, 0, "rtvd"),
+                                            ("waf_hllc_fp32", H.WAF, H.PLM, H.RS_HLLC, 0, "waf")) \
+                if "schemes" in legs else ():
             p = make_params(H, H.FP32, dx)
             p.scheme, p.recon, p.riemann, p.characteristic = sch, rec, rs, ch
             bx = RT.UniformBox(U, p, cfl=CFL, device=dev, stream=stream)
-            tb = bx.tune()
+            if args.block_threads:
+                # a fixed launch shape (profiling): no tuning launches
+                bx.p.block_threads = min(args.block_threads, H.hydro_max_block_threads(bx.p))
+                tb = {"block_threads": bx.p.block_threads}
+            else:
+                tb = bx.tune()
             bx.compute_dt()
             sm, am, tm, _ = time_box(bx, 50, 3, torch)
             extra[tag] = {"value": cells * 50 / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / 50,
-                          "kernel_ms": am, "block_threads": tb["block_threads"]}
+                          "kernel_ms": am, "block_threads": tb["block_threads"],
+                          "roofline": leg_roofline(fkey, am, peak, fp32_note)}
             del bx
         torch.cuda.empty_cache()
         if "amr_levels" in legs:
@@ -524,8 +545,9 @@ def main():
                 "config": dict(CONFIG, parallelism="replicas%d" % world if world > 1 else "single GPU"),
                 "p50_step_ms": RT.percentile(step_ms, 50), "p99_step_ms": RT.percentile(step_ms, 99),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 3 * args.steps, "autotuned": {"block_threads": tuned["block_threads"],
-                                                              "grid_ctas": tuned["grid_ctas"]}, "status_error_groups": int(np.count_nonzero(st & H.ST_ERROR_MASK)),
+                "gpu_launches": 3 * args.steps,
+                "autotuned": {"block_threads": tuned["block_threads"], "grid_ctas": tuned["grid_ctas"]},
+                "status_error_groups": int(np.count_nonzero(st & H.ST_ERROR_MASK)),
                 "state_finite": finite, "extra": extra,
                 "paper_context": "3.0e7 cell-updates/s, CTU+PPM+Roe FP32 on one Tesla C2050 incl. transfers "
                                  "(Sec. 3.2); other hardware, not a target"}

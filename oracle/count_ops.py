@@ -18,7 +18,13 @@ cell needs on an unbounded grid with nothing recomputed:
        reconstructions, 1 prediction, 3 Riemann solves;
   VL : 7 conversions (1 U->W of the half step, 6 face W->U), 15
        reconstructions, 1 prediction, 6 Riemann solves (3 first-order + 3);
-plus the update, counted per cell.  Flops = additions + multiplications +
+plus the update, counted per cell.  The directionally split schemes sweep
+each cell once per direction; per cell and sweep:
+  RTVD: 2 flux splittings (U^n and the half step), 1 first-order flux
+       difference, 1 half step, 1 limited flux, 1 update;
+  WAF : 1 side state, 1 HLLC wave fan, 1 weighted-average flux, 1 update.
+CTU with characteristic reconstruction: as CTU, but one reconstruction per
+direction (all 5 waves, with the projections) instead of one per variable.  Flops = additions + multiplications +
 divisions + square roots + powers; comparisons / min / max / abs are reported
 apart ("cmp").  The halo recomputation a patch group actually does on top is
 therefore not credited.
@@ -42,18 +48,21 @@ MIN_CALLS = {
     O.CTU: {"eos": 7, "recon": 15, "trace": 3, "riemann": 6, "correct": 3},
     O.MHM: {"eos": 13, "recon": 15, "predict": 1, "riemann": 3},
     O.VL: {"eos": 7, "recon": 15, "predict": 1, "riemann": 6},
+    O.RTVD: {"eos": 6, "riemann": 3, "predict": 3, "recon": 3, "update": 3},
+    O.WAF: {"eos": 3, "riemann": 3, "recon": 3, "update": 3},
 }
-SCHEME_NAMES = {O.MHM: "mhm", O.VL: "vl", O.CTU: "ctu"}
+SCHEME_NAMES = {O.MHM: "mhm", O.VL: "vl", O.CTU: "ctu", O.RTVD: "rtvd", O.WAF: "waf"}
 RECON_NAMES = {O.PLM: "plm", O.PPM: "ppm"}
 SOLVER_NAMES = {O.EXACT: "exact", O.HLLE: "hlle", O.HLLC: "hllc", O.ROE: "roe"}
 
 
-def count(scheme, recon, rs, groups):
+def count(scheme, recon, rs, groups, characteristic=0):
     N = 16
     tot = {s: {c: 0 for c in O.OPCLASSES} for s in O.SECTIONS}
     calls = {s: 0 for s in O.SECTIONS}
     for Ug, dt, dx in groups:
-        P = O.Params(scheme=scheme, recon=recon, riemann=rs, limiter=O.MINMOD, dt=dt, dx=dx)
+        P = O.Params(scheme=scheme, recon=recon, riemann=rs, limiter=O.MINMOD, dt=dt, dx=dx,
+                     characteristic=characteristic)
         ops, cl = O.count_ops(P, Ug, N)
         for s in O.SECTIONS:
             calls[s] += cl[s]
@@ -62,12 +71,16 @@ def count(scheme, recon, rs, groups):
     per_cell = {}
     cmp_cell = 0.0
     ng = len(groups)
-    for s, k in MIN_CALLS[scheme].items():
+    need = dict(MIN_CALLS[scheme])
+    if characteristic:
+        need["recon"] = 3
+    for s, k in need.items():
         f = sum(tot[s][c] for c in FLOP) / calls[s]
         per_cell[s] = k * f
         cmp_cell += k * tot[s]["cmp"] / calls[s]
-    per_cell["update"] = sum(tot["update"][c] for c in FLOP) / (ng * N ** 3)
-    cmp_cell += tot["update"]["cmp"] / (ng * N ** 3)
+    if "update" not in need:
+        per_cell["update"] = sum(tot["update"][c] for c in FLOP) / (ng * N ** 3)
+        cmp_cell += tot["update"]["cmp"] / (ng * N ** 3)
     executed = sum(sum(tot[s][c] for c in FLOP) for s in O.SECTIONS) / (ng * N ** 3)
     div_sqrt = {c: sum(tot[s][c] for s in O.SECTIONS) / (ng * N ** 3) for c in ("div", "sqrt", "pow")}
     return {"flops": sum(per_cell.values()), "by_section": per_cell, "cmp": cmp_cell,
@@ -90,6 +103,18 @@ def main():
                 key = "%s-%s-%s" % (SCHEME_NAMES[scheme], RECON_NAMES[recon], SOLVER_NAMES[rs])
                 table["entries"][key] = count(scheme, recon, rs, groups)
                 print(key, round(table["entries"][key]["flops"], 1))
+    g = O.required_ghost(O.CTU, O.PPM)
+    Ug = O.gather(U, W.group_origins(n, n, n, N), N, g, bc=0)
+    groups = [(Ug[i], dt, dx) for i in range(0, Ug.shape[0], 3)]
+    table["entries"]["ctu-ppm-roe-char"] = count(O.CTU, O.PPM, O.ROE, groups, characteristic=1)
+    print("ctu-ppm-roe-char", round(table["entries"]["ctu-ppm-roe-char"]["flops"], 1))
+    for scheme in (O.RTVD, O.WAF):
+        g = O.required_ghost(scheme, 0)
+        Ug = O.gather(U, W.group_origins(n, n, n, N), N, g, bc=0)
+        groups = [(Ug[i], dt, dx) for i in range(0, Ug.shape[0], 3)]
+        key = SCHEME_NAMES[scheme]
+        table["entries"][key] = count(scheme, O.PLM, O.HLLC, groups)
+        print(key, round(table["entries"][key]["flops"], 1))
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
     with open(OUT, "w") as fh:
         json.dump(table, fh, indent=1, sort_keys=True)

@@ -236,6 +236,8 @@ int orc_count_ops(const OrcParams* p, const double* U_in, int N, int g, long lon
   P.gas.pres_floor = p->pres_floor;
   P.dt = p->dt;
   for (int d = 0; d < 3; ++d) P.dx[d] = p->dx[d];
+  P.characteristic = p->characteristic;
+  P.split_order = p->split_order;
   Box B(N, g);
   std::vector<Counted> Uin(5 * B.M3), Uout(5L * N * N * N), fl(30L * N * N);
   for (long i = 0; i < 5 * B.M3; ++i) Uin[i] = Counted(U_in[i]);

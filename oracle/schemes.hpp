@@ -474,15 +474,27 @@ inline void rtvd_row(const Params<R>& P, std::vector<std::array<R, 5>>& u, int l
                      R Flo[5], R Fhi[5]) {
   const int n = (int)u.size();
   std::vector<std::array<R, 5>> FR(n), FL(n), F1(n), FRh(n), FLh(n), FT(n);
-  for (int j = lo - 3; j < hi + 3; ++j) rtvd_split(u[j].data(), P.gas, FR[j].data(), FL[j].data());
-  for (int j = lo - 3; j < hi + 2; ++j)
+  // (operation-count scopes: per cell two splittings, one first-order flux
+  // difference, one half step, one limited flux, one update)
+  for (int j = lo - 3; j < hi + 3; ++j) {
+    Sec<R> sec(SEC_EOS);
+    rtvd_split(u[j].data(), P.gas, FR[j].data(), FL[j].data());
+  }
+  for (int j = lo - 3; j < hi + 2; ++j) {
+    Sec<R> sec(SEC_RIEMANN);
     for (int v = 0; v < 5; ++v) F1[j][v] = FR[j][v] - FL[j + 1][v];
+  }
   for (int j = lo - 2; j < hi + 2; ++j) {
     R uh[5];
-    for (int v = 0; v < 5; ++v) uh[v] = u[j][v] - hdtdx * (F1[j][v] - F1[j - 1][v]);
+    {
+      Sec<R> sec(SEC_PREDICT);
+      for (int v = 0; v < 5; ++v) uh[v] = u[j][v] - hdtdx * (F1[j][v] - F1[j - 1][v]);
+    }
+    Sec<R> sec(SEC_EOS);
     rtvd_split(uh, P.gas, FRh[j].data(), FLh[j].data());
   }
-  for (int i = lo - 1; i < hi; ++i)
+  for (int i = lo - 1; i < hi; ++i) {
+    Sec<R> sec(SEC_RECON);
     for (int v = 0; v < 5; ++v) {
       R fr = FRh[i][v] + R(0.5) * limited_slope(P.limiter, P.theta, FRh[i][v] - FRh[i - 1][v],
                                                 FRh[i + 1][v] - FRh[i][v]);
@@ -490,8 +502,11 @@ inline void rtvd_row(const Params<R>& P, std::vector<std::array<R, 5>>& u, int l
                                                     FLh[i + 2][v] - FLh[i + 1][v]);
       FT[i][v] = fr - fl;
     }
-  for (int i = lo; i < hi; ++i)
+  }
+  for (int i = lo; i < hi; ++i) {
+    Sec<R> sec(SEC_UPDATE);
     for (int v = 0; v < 5; ++v) u[i][v] = u[i][v] - dtdx * (FT[i][v] - FT[i - 1][v]);
+  }
   for (int v = 0; v < 5; ++v) {
     Flo[v] = FT[lo - 1][v];
     Fhi[v] = FT[hi - 1][v];
@@ -556,9 +571,18 @@ inline void waf_row(const Params<R>& P, std::vector<std::array<R, 5>>& u, int lo
   std::vector<Side<R>> sd(n);
   std::vector<Fan<R>> fan(n);
   std::vector<std::array<R, 5>> FW(n);
-  for (int j = lo - 2; j < hi + 2; ++j) make_side(u[j].data(), P.gas, sd[j]);
-  for (int j = lo - 2; j < hi + 1; ++j) hllc_fan(sd[j], sd[j + 1], P.gas, fan[j]);  // face j + 1/2
+  // (operation-count scopes: per cell one side state, one wave fan, one
+  // weighted flux, one update)
+  for (int j = lo - 2; j < hi + 2; ++j) {
+    Sec<R> sec(SEC_EOS);
+    make_side(u[j].data(), P.gas, sd[j]);
+  }
+  for (int j = lo - 2; j < hi + 1; ++j) {
+    Sec<R> sec(SEC_RIEMANN);
+    hllc_fan(sd[j], sd[j + 1], P.gas, fan[j]);  // face j + 1/2
+  }
   for (int i = lo - 1; i < hi; ++i) {
+    Sec<R> sec(SEC_RECON);
     const Fan<R>& f = fan[i];
     R F[5];
     for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (f.F[0][v] + f.F[3][v]);
@@ -574,8 +598,10 @@ inline void waf_row(const Params<R>& P, std::vector<std::array<R, 5>>& u, int lo
     }
     for (int v = 0; v < 5; ++v) FW[i][v] = F[v];
   }
-  for (int i = lo; i < hi; ++i)
+  for (int i = lo; i < hi; ++i) {
+    Sec<R> sec(SEC_UPDATE);
     for (int v = 0; v < 5; ++v) u[i][v] = u[i][v] - dtdx * (FW[i][v] - FW[i - 1][v]);
+  }
   for (int v = 0; v < 5; ++v) {
     Flo[v] = FW[lo - 1][v];
     Fhi[v] = FW[hi - 1][v];

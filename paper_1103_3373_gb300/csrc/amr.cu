@@ -210,7 +210,7 @@ template <int G> struct StageBox {
 // and neighbours as the wrapped one (periodic); at an outflow edge both give
 // a zero slope along the clamped axis.
 template <class S, int G>
-__global__ void __launch_bounds__(AMR_PREP_THREADS)
+__global__ void __launch_bounds__(AMR_PREP_THREADS, 2)
     amr_prepare_staged(LevelView F, LevelView C, const S* __restrict__ cnew, S theta, int bc, S* __restrict__ out,
                        unsigned* err) {
   constexpr int M = AN + 2 * G;
@@ -260,46 +260,65 @@ __global__ void __launch_bounds__(AMR_PREP_THREADS)
       const int b = r / M, a = r - b * M;
       const int fu = ox + a - G, fv = oy + b - G;  // unwrapped fine x, y
       const int fx = amr_cell(fu, F.X, bc), fy = amr_cell(fv, F.Y, bc);
-      for (int c = 0; c < M; ++c) {
-        const int fw = oz + c - G;
-        const int fz = amr_cell(fw, F.Z, bc);
-        S* o = base + (long long)c * M * M + r;
-        const int g = group_at(F, fx, fy, fz);
-        if (g >= 0) {
-          const S* s = Uf + (long long)g * 5 * N3 + ((fz % AN) * AN + fy % AN) * AN + fx % AN;
+      // the column's fine cells lie in at most three groups of the level:
+      // below the group (c < G), beside it (G <= c < G + AN), above it
+      int gseg[3];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) o[v * M3] = s[v * N3];
-          continue;
-        }
-        const int ci = (fu >> 1) - cx0, cj = (fv >> 1) - cy0, ck = (fw >> 1) - cz0;  // 1 .. CB-2
-        const int idx = (ck * CB + cj) * CB + ci;
-        const int st[3] = {1, CB, CB * CB};
-        bool ok = okp[idx] != 0;
+      for (int s = 0; s < 3; ++s)
+        gseg[s] = group_at(F, fx, fy, amr_cell(oz + (s == 0 ? -1 : (s == 1 ? 0 : AN)), F.Z, bc));
+      const long long xy = (long long)(fy % AN) * AN + fx % AN;
+      // CU cells at a time: every load of the batch is issued before its stores
+      constexpr int CU = sizeof(S) == 4 ? 4 : 2;
+      for (int c0 = 0; c0 < M; c0 += CU) {
+        S val[CU][5];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) ok = ok && okp[idx + st[d]] != 0 && okp[idx - st[d]] != 0;
-        S acc[5];
-        if (ok) {
-          const int fc[3] = {fx, fy, fz};
+        for (int q = 0; q < CU; ++q) {
+          const int c = c0 + q;
+          if (c >= M) break;
+          const int fw = oz + c - G;
+          const int fz = amr_cell(fw, F.Z, bc);
+          const int g = gseg[c < G ? 0 : (c < G + AN ? 1 : 2)];
+          if (g >= 0) {
+            const S* s = Uf + (long long)g * 5 * N3 + (long long)(fz % AN) * AN * AN + xy;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) acc[v] = cs[v * CB3 + idx];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const S q = (fc[d] & 1) ? S(0.25) : S(-0.25);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              const S uc = cs[v * CB3 + idx];
-              const S uu = cs[v * CB3 + idx + st[d]];
-              const S ud = cs[v * CB3 + idx - st[d]];
-              acc[v] = acc[v] + q * minmod(uu - uc, uc - ud);
-            }
+            for (int v = 0; v < 5; ++v) val[q][v] = s[v * N3];
+            continue;
           }
-        } else {
-          raise_err(err, HYDRO_AMR_ENESTING);
+          const int ci = (fu >> 1) - cx0, cj = (fv >> 1) - cy0, ck = (fw >> 1) - cz0;  // 1 .. CB-2
+          const int idx = (ck * CB + cj) * CB + ci;
+          const int st[3] = {1, CB, CB * CB};
+          bool ok = okp[idx] != 0;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) acc[v] = S(NAN);
+          for (int d = 0; d < 3; ++d) ok = ok && okp[idx + st[d]] != 0 && okp[idx - st[d]] != 0;
+          if (ok) {
+            const int fc[3] = {fx, fy, fz};
+#pragma unroll
+            for (int v = 0; v < 5; ++v) val[q][v] = cs[v * CB3 + idx];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              const S h = (fc[d] & 1) ? S(0.25) : S(-0.25);
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                const S uc = cs[v * CB3 + idx];
+                const S uu = cs[v * CB3 + idx + st[d]];
+                const S ud = cs[v * CB3 + idx - st[d]];
+                val[q][v] = val[q][v] + h * minmod(uu - uc, uc - ud);
+              }
+            }
+          } else {
+            raise_err(err, HYDRO_AMR_ENESTING);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) val[q][v] = S(NAN);
+          }
         }
 #pragma unroll
-        for (int v = 0; v < 5; ++v) o[v * M3] = acc[v];
+        for (int q = 0; q < CU; ++q) {
+          const int c = c0 + q;
+          if (c >= M) break;
+          S* o = base + (long long)c * M * M + r;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) o[v * M3] = val[q][v];
+        }
       }
     }
     __syncthreads();  // the window is reused by the CTA's next group
