@@ -78,6 +78,17 @@ cudaError_t copy_planes(void* dst, const void* src, const hydro_pipeline* h, int
   return cudaMemcpy2DAsync((char*)dst + off, pitch, (const char*)src + off, pitch, plane * (z1 - z0), 5, kind, st);
 }
 
+// An error after some work was enqueued: the caller's stream waits for the
+// pipeline's streams (what was enqueued completes before later work there),
+// and the next step starts unchained.
+int fail(hydro_pipeline* h, cudaStream_t user, int rc) {
+  h->has_prev = false;
+  cudaStream_t ss[4] = {h->s_in, h->s_comp[0], h->s_comp[1], h->s_out};
+  for (cudaStream_t s : ss)
+    if (cudaEventRecord(h->ev_done, s) == cudaSuccess) cudaStreamWaitEvent(user, h->ev_done, 0);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -146,6 +157,11 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   const int need = hydro_required_ghost(p->scheme, p->recon);
   if (need < 0 || need > h->ghost) return HYDRO_EINVAL;
   if (p->precision < HYDRO_FP64 || p->precision > HYDRO_FP32_MIXED) return HYDRO_EINVAL;
+  // scratch of both compute streams and of the reduction, before any work
+  const size_t need_ws = hydro_workspace_bytes(p, h->N);
+  if (need_ws && (!p->workspace || p->workspace_bytes < need_ws || !ws2 || ws2_bytes < need_ws))
+    return HYDRO_EWORKSPACE;
+  if (!red_ws || red_ws_bytes < hydro_cfl_workspace_bytes()) return HYDRO_EWORKSPACE;
   const size_t es = p->precision == HYDRO_FP64 ? sizeof(double) : sizeof(float);
   const long long XYZ = (long long)h->X * h->Y * h->Z;
   cudaStream_t user = (cudaStream_t)stream;
@@ -178,7 +194,7 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[s], h->s_in);
   }
-  if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  if (e != cudaSuccess) return fail(h, user, hyd::record_cuda_error(e));
   // advance each slab when its input is in; return it at once
   hydro_params p2 = *p;
   p2.workspace = ws2;
@@ -187,24 +203,24 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   for (int s = 0; s < h->nslab; ++s) {
     const int k = s & 1;
     e = cudaStreamWaitEvent(c[k], h->ev_in[s], 0);
-    if (e != cudaSuccess) return hyd::record_cuda_error(e);
+    if (e != cudaSuccess) return fail(h, user, hyd::record_cuda_error(e));
     int rc = hydro_advance_uniform_zrange(pc[k], dev_in, dev_out, h->X, h->Y, h->Z, h->N, h->bc, h->zb[s],
                                           h->zb[s + 1], flux, dev_status, c[k]);
-    if (rc != HYDRO_OK) return rc;
+    if (rc != HYDRO_OK) return fail(h, user, rc);
     e = cudaEventRecord(h->ev_comp[s], c[k]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_comp[s], 0);
     if (e == cudaSuccess)
       e = copy_planes(host_out, dev_out, h, h->zb[s], h->zb[s + 1], es, cudaMemcpyDeviceToHost, h->s_out);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[s], h->s_out);
-    if (e != cudaSuccess) return hyd::record_cuda_error(e);
+    if (e != cudaSuccess) return fail(h, user, hyd::record_cuda_error(e));
   }
   // next dt from the whole new state, after both compute streams
   e = cudaEventRecord(h->ev_c1, c[1]);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c[0], h->ev_c1, 0);
-  if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  if (e != cudaSuccess) return fail(h, user, hyd::record_cuda_error(e));
   int rc = hydro_cfl_dt(dev_out, 1, 5 * XYZ, XYZ, XYZ, p->precision, p->gamma, p->dens_floor, p->pres_floor, p->dx,
                         cfl, const_cast<double*>(p->dt_dev), nullptr, red_ws, red_ws_bytes, c[0]);
-  if (rc != HYDRO_OK) return rc;
+  if (rc != HYDRO_OK) return fail(h, user, rc);
   // dt to the host on the same stream, before the next step's reduction can
   // overwrite it (the next step's advances wait for ev_cfl)
   if (host_dt) e = cudaMemcpyAsync(host_dt, p->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, c[0]);
@@ -213,7 +229,7 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   // the caller's stream resumes after the copies out (which follow everything)
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_done, h->s_out);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->ev_done, 0);
-  if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  if (e != cudaSuccess) return fail(h, user, hyd::record_cuda_error(e));
   h->has_prev = true;
   h->prev_host_out = host_out;
   h->prev_dev_in = dev_in;

@@ -164,3 +164,18 @@ def test_pipeline_argument_errors(torch_dev):
     with pytest.raises(H.HydroError):                    # PPM + CTU needs 3 ghost layers, planned for 2
         pipe.step(p, a, b, da, db, 0.4, ws)
     pipe.close()
+    # FP64 kernels keep their rings in scratch: the second compute stream's
+    # is required, checked before any work is enqueued
+    pipe = H.Pipeline(32, 32, 64, 3, slabs=2)
+    p64 = H.Params(scheme=H.CTU, recon=H.PPM, riemann=H.RS_ROE, precision=H.FP64, dx=(0.1,) * 3,
+                   dt_dev=torch.zeros(1, dtype=torch.float64, device=dev))
+    n = H.hydro_workspace_bytes(p64)
+    assert n > 0
+    p64.workspace = torch.empty(n, dtype=torch.uint8, device=dev)
+    a64 = torch.zeros((5, 64, 32, 32), dtype=torch.float64).pin_memory()
+    b64 = torch.zeros_like(a64).pin_memory()
+    da64 = torch.zeros((5, 64, 32, 32), dtype=torch.float64, device=dev)
+    with pytest.raises(H.HydroError) as ei:
+        pipe.step(p64, a64, b64, da64, torch.zeros_like(da64), 0.4, ws)
+    assert ei.value.code == H.EWORKSPACE
+    pipe.close()
