@@ -126,7 +126,7 @@ __global__ void cfl_partial_kernel(const S* __restrict__ U, int G, long long gst
   if (threadIdx.x == 0) anybad = 0;
   S m[3] = {S(0), S(0), S(0)};
   bool bad = false;
-  Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor};
+  Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor, (S)(1.0 / (gamma - 1.0))};
   if constexpr (VEC) {
     using VT = Vec16<S>;
     constexpr int W = VT::W;

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
   Opts<T> o;
   o.gas.gamma = (T)kc.gamma;
   o.gas.gm1 = (T)(kc.gamma - 1.0);
+  o.gas.igm1 = (T)(1.0 / (kc.gamma - 1.0));
   o.gas.dens_floor = (T)kc.dens_floor;
   o.gas.pres_floor = (T)kc.pres_floor;
   o.theta = (T)kc.theta;

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS)
   long long end = begin + NOALLOC_CELLS_PER_CTA;
   if (end > total) end = total;
   if (threadIdx.x == 0) anybad = 0;
-  hyd::Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor};
+  hyd::Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor, (S)(1.0 / (gamma - 1.0))};
   S m[3] = {S(0), S(0), S(0)};
   bool bad = false;
   for (long long e = begin + threadIdx.x; e < end; e += NOALLOC_THREADS) {

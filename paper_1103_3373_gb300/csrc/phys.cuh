@@ -43,6 +43,17 @@ template <class T> struct Gas {
   T gm1;         // gamma - 1
   T dens_floor;  // floors, applied as max(q, floor)
   T pres_floor;
+  T igm1;        // 1 / (gamma - 1)
+};
+
+// FP32 forms: a denominator used more than once (rho, c^2, gamma - 1) is
+// inverted once and multiplied by; the FP64 form divides at every use, in the
+// operation order its bit-for-bit parity with the FP64 oracle rests on.
+template <class T> struct FastRcp {
+  static constexpr bool on = false;
+};
+template <> struct FastRcp<float> {
+  static constexpr bool on = true;
 };
 
 // Options a kernel reads at run time (uniform over the launch).
@@ -92,10 +103,17 @@ template <int D, class T> __device__ __forceinline__ void rot_out(const T b[5], 
 // MIXED: when U4 - kin has lost more than 10 bits to cancellation, the
 // internal energy is recomputed in FP64.
 template <class T, bool MIXED>
-__device__ __forceinline__ void prim(const T U[5], T W[5], const Gas<T>& g) {
+__device__ __forceinline__ void prim(const T U[5], T W[5], const Gas<T>& g, T* irho = nullptr) {
   T rho = U[0];
   if (rho < g.dens_floor) rho = g.dens_floor;
-  T kin = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho;
+  T ir = T(0);
+  T kin;
+  if constexpr (FastRcp<T>::on) {
+    ir = T(1) / rho;
+    kin = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir;
+  } else {
+    kin = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho;
+  }
   T eint = U[4] - kin;
   if (MIXED) {
     if (eint < T(1.0 / 1024.0) * U[4]) {
@@ -107,9 +125,16 @@ __device__ __forceinline__ void prim(const T U[5], T W[5], const Gas<T>& g) {
   T p = g.gm1 * eint;
   if (p < g.pres_floor) p = g.pres_floor;
   W[0] = rho;
-  W[1] = U[1] / rho;
-  W[2] = U[2] / rho;
-  W[3] = U[3] / rho;
+  if constexpr (FastRcp<T>::on) {
+    W[1] = U[1] * ir;
+    W[2] = U[2] * ir;
+    W[3] = U[3] * ir;
+    if (irho) *irho = ir;
+  } else {
+    W[1] = U[1] / rho;
+    W[2] = U[2] / rho;
+    W[3] = U[3] / rho;
+  }
   W[4] = p;
 }
 
@@ -119,7 +144,11 @@ template <class T> __device__ __forceinline__ void cons(const T W[5], T U[5], co
   U[1] = W[0] * W[1];
   U[2] = W[0] * W[2];
   U[3] = W[0] * W[3];
-  U[4] = W[4] / g.gm1 + T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  const T ke = T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  if constexpr (FastRcp<T>::on)
+    U[4] = W[4] * g.igm1 + ke;
+  else
+    U[4] = W[4] / g.gm1 + ke;
 }
 
 // Physical flux along the local normal of local primitives W with energy E.
@@ -217,9 +246,30 @@ template <class T> struct Eig {
   T i2cc;  // (2 c) c
   T cc;    // c c
   T cor;   // c / rho
+  T icc;   // 1 / (c c)      (FP32 forms)
+  T hicc;  // 1 / ((2 c) c)  (FP32 forms)
 };
 
 template <class T> __device__ __forceinline__ void eig(const T W[5], const Gas<T>& g, Eig<T>& e) {
+  if constexpr (FastRcp<T>::on) {
+    const T ir = T(1) / W[0];
+    const T c = sqrtv(g.gamma * W[4] * ir);
+    const T ic = T(1) / c;
+    e.rho = W[0];
+    e.c = c;
+    e.lam[0] = W[1] - c;
+    e.lam[1] = W[1];
+    e.lam[2] = W[1];
+    e.lam[3] = W[1];
+    e.lam[4] = W[1] + c;
+    e.r2c = T(0.5) * W[0] * ic;
+    e.cc = c * c;
+    e.i2cc = T(2) * e.cc;
+    e.cor = c * ir;
+    e.icc = ic * ic;
+    e.hicc = T(0.5) * e.icc;
+    return;
+  }
   T c = csound(W[0], W[4], g);
   e.rho = W[0];
   e.c = c;
@@ -236,6 +286,13 @@ template <class T> __device__ __forceinline__ void eig(const T W[5], const Gas<T
 
 // l_a . X   (a = 0..4)
 template <class T> __device__ __forceinline__ T lproj(const Eig<T>& e, int a, const T X[5]) {
+  if constexpr (FastRcp<T>::on) {
+    if (a == 0) return -e.r2c * X[1] + X[4] * e.hicc;
+    if (a == 1) return X[0] - X[4] * e.icc;
+    if (a == 2) return X[2];
+    if (a == 3) return X[3];
+    return e.r2c * X[1] + X[4] * e.hicc;
+  }
   if (a == 0) return -e.r2c * X[1] + X[4] / e.i2cc;
   if (a == 1) return X[0] - X[4] / e.cc;
   if (a == 2) return X[2];
@@ -344,13 +401,17 @@ __device__ __forceinline__ void trace_ppm(const T W0[5], const T WL[5], const T 
 // physical flux F.
 template <class T> struct Side {
   T U[5], W[5], c, F[5];
+  T ir;  // 1 / rho (FP32 forms)
 };
 
 template <class T, bool MIXED> __device__ __forceinline__ void mkside(const T U[5], const Gas<T>& g, Side<T>& s) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) s.U[v] = U[v];
-  prim<T, MIXED>(U, s.W, g);
-  s.c = csound(s.W[0], s.W[4], g);
+  prim<T, MIXED>(U, s.W, g, &s.ir);
+  if constexpr (FastRcp<T>::on)
+    s.c = sqrtv(g.gamma * s.W[4] * s.ir);
+  else
+    s.c = csound(s.W[0], s.W[4], g);
   pflux(s.W, U[4], s.F);
 }
 
@@ -365,8 +426,14 @@ template <class T> __device__ __forceinline__ void ravg(const Side<T>& L, const 
   A.u = (sL * L.W[1] + sR * R.W[1]) * inv;
   A.v = (sL * L.W[2] + sR * R.W[2]) * inv;
   A.w = (sL * L.W[3] + sR * R.W[3]) * inv;
-  T HL = (L.U[4] + L.W[4]) / L.W[0];
-  T HR = (R.U[4] + R.W[4]) / R.W[0];
+  T HL, HR;
+  if constexpr (FastRcp<T>::on) {
+    HL = (L.U[4] + L.W[4]) * L.ir;
+    HR = (R.U[4] + R.W[4]) * R.ir;
+  } else {
+    HL = (L.U[4] + L.W[4]) / L.W[0];
+    HR = (R.U[4] + R.W[4]) / R.W[0];
+  }
   A.H = (sL * HL + sR * HR) * inv;
   A.q2 = A.u * A.u + A.v * A.v + A.w * A.w;
   A.a2 = g.gm1 * (A.H - T(0.5) * A.q2);
@@ -487,6 +554,8 @@ __device__ __noinline__ Flux5<T> exact_flux(V5<T> WLv, V5<T> WRv, T cL, T cR, T 
   }
   L.c = cL;
   R.c = cR;
+  L.ir = T(1) / L.W[0];
+  R.ir = T(1) / R.W[0];
   L.U[0] = L.W[0]; L.U[1] = L.W[0] * L.W[1]; L.U[2] = L.W[0] * L.W[2]; L.U[3] = L.W[0] * L.W[3]; L.U[4] = EL;
   R.U[0] = R.W[0]; R.U[1] = R.W[0] * R.W[1]; R.U[2] = R.W[0] * R.W[2]; R.U[3] = R.W[0] * R.W[3]; R.U[4] = ER;
   T gam = g.gamma;
@@ -719,7 +788,10 @@ template <class T> __device__ __forceinline__ void cons_local(const T W[5], int 
   U[1] = W[0] * W[1];
   U[2] = W[0] * W[2];
   U[3] = W[0] * W[3];
-  U[4] = W[4] / g.gm1 + T(0.5) * W[0] * ke;
+  if constexpr (FastRcp<T>::on)
+    U[4] = W[4] * g.igm1 + T(0.5) * W[0] * ke;
+  else
+    U[4] = W[4] / g.gm1 + T(0.5) * W[0] * ke;
 }
 
 }  // namespace hyd
