@@ -71,6 +71,13 @@ __device__ __forceinline__ float sqrtv(float a) { return sqrtf(a); }
 __device__ __forceinline__ double powv(double a, double b) { return pow(a, b); }
 __device__ __forceinline__ float powv(float a, float b) { return powf(a, b); }
 __device__ __forceinline__ bool isnanv(double a) { return isnan(a); }
+// a / b.  FP64 divides (IEEE).  The FP32 forms use the fast division
+// intrinsic (2 ulp for 2^-126 <= |b| <= 2^126), which covers every
+// denominator it is used on: densities, sound speeds, Roe-averaged c^2,
+// wave-speed differences, limiter sums and constants.  It is not used in
+// the exact solver's Newton iteration.
+__device__ __forceinline__ double divv(double a, double b) { return a / b; }
+__device__ __forceinline__ float divv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ bool isnanv(float a) { return isnan(a); }
 
 // Directions are compile-time constants everywhere so that the 5-vectors stay
@@ -109,7 +116,7 @@ __device__ __forceinline__ void prim(const T U[5], T W[5], const Gas<T>& g, T* i
   T ir = T(0);
   T kin;
   if constexpr (FastRcp<T>::on) {
-    ir = T(1) / rho;
+    ir = divv(T(1), rho);
     kin = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir;
   } else {
     kin = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho;
@@ -148,7 +155,7 @@ template <class T> __device__ __forceinline__ void cons(const T W[5], T U[5], co
   if constexpr (FastRcp<T>::on)
     U[4] = W[4] * g.igm1 + ke;
   else
-    U[4] = W[4] / g.gm1 + ke;
+    U[4] = divv(W[4], g.gm1) + ke;
 }
 
 // Physical flux along the local normal of local primitives W with energy E.
@@ -161,7 +168,9 @@ template <class T> __device__ __forceinline__ void pflux(const T W[5], T E, T F[
   F[4] = (E + W[4]) * W[1];
 }
 
-template <class T> __device__ __forceinline__ T csound(T rho, T p, const Gas<T>& g) { return sqrtv(g.gamma * p / rho); }
+template <class T> __device__ __forceinline__ T csound(T rho, T p, const Gas<T>& g) {
+  return sqrtv(divv(g.gamma * p, rho));
+}
 
 // ------------------------------------------------------------- limiters
 // dL = w_i - w_{i-1}, dR = w_{i+1} - w_i; 0 unless dL*dR > 0;
@@ -185,9 +194,9 @@ template <int LIM = -1, class T> __device__ __forceinline__ T slope(int lim, T t
   T dC = T(0.5) * (dL + dR);
   T r;
   if (lim == LIM_VANLEER) {
-    r = T(2) * prod / (dL + dR);
+    r = divv(T(2) * prod, dL + dR);
   } else if (lim == LIM_VANALBADA) {
-    r = prod * (dL + dR) / (dL * dL + dR * dR);
+    r = divv(prod * (dL + dR), dL * dL + dR * dR);
   } else {
     T m = absv(theta * dL);
     T b = absv(theta * dR);
@@ -195,7 +204,7 @@ template <int LIM = -1, class T> __device__ __forceinline__ T slope(int lim, T t
     m = b < m ? b : m;
     m = c < m ? c : m;
     if (lim == LIM_HYBRID) {
-      T e = absv(T(2) * prod / (dL + dR));
+      T e = absv(divv(T(2) * prod, dL + dR));
       m = e < m ? e : m;
     }
     r = dC > T(0) ? m : -m;
@@ -219,8 +228,8 @@ __device__ __forceinline__ void ppm(T wmm, T wm, T w0, T wp, T wpp, int lim, T t
   T dm = slope<LIM>(lim, theta, wm - wmm, w0 - wm);
   T d0 = slope<LIM>(lim, theta, w0 - wm, wp - w0);
   T dp = slope<LIM>(lim, theta, wp - w0, wpp - wp);
-  T L = T(0.5) * (wm + w0) - (d0 - dm) / T(6);
-  T R = T(0.5) * (w0 + wp) - (dp - d0) / T(6);
+  T L = T(0.5) * (wm + w0) - divv(d0 - dm, T(6));
+  T R = T(0.5) * (w0 + wp) - divv(dp - d0, T(6));
   // constraints as selects: local extremum -> flat; overshoot -> move one edge
   const bool ext = (R - w0) * (w0 - L) <= T(0);
   T dA = R - L;
@@ -252,9 +261,9 @@ template <class T> struct Eig {
 
 template <class T> __device__ __forceinline__ void eig(const T W[5], const Gas<T>& g, Eig<T>& e) {
   if constexpr (FastRcp<T>::on) {
-    const T ir = T(1) / W[0];
+    const T ir = divv(T(1), W[0]);
     const T c = sqrtv(g.gamma * W[4] * ir);
-    const T ic = T(1) / c;
+    const T ic = divv(T(1), c);
     e.rho = W[0];
     e.c = c;
     e.lam[0] = W[1] - c;
@@ -422,7 +431,7 @@ template <class T> struct RAvg {
 template <class T> __device__ __forceinline__ void ravg(const Side<T>& L, const Side<T>& R, const Gas<T>& g, RAvg<T>& A) {
   T sL = sqrtv(L.W[0]);
   T sR = sqrtv(R.W[0]);
-  T inv = T(1) / (sL + sR);
+  T inv = divv(T(1), sL + sR);
   A.u = (sL * L.W[1] + sR * R.W[1]) * inv;
   A.v = (sL * L.W[2] + sR * R.W[2]) * inv;
   A.w = (sL * L.W[3] + sR * R.W[3]) * inv;
@@ -459,7 +468,7 @@ template <class T> __device__ __forceinline__ void hlle(const Side<T>& L, const 
   einfeldt(L, R, g, SL, SR);
   T bp = SR > T(0) ? SR : T(0);
   T bm = SL < T(0) ? SL : T(0);
-  T inv = T(1) / (bp - bm);
+  T inv = divv(T(1), bp - bm);
 #pragma unroll
   for (int v = 0; v < 5; ++v) F[v] = (bp * L.F[v] - bm * R.F[v] + bp * bm * (R.U[v] - L.U[v])) * inv;
 }
@@ -473,7 +482,7 @@ template <class T> __device__ __forceinline__ void hllc(const Side<T>& L, const 
   einfeldt(L, R, g, SL, SR);
   T mL = L.W[0] * (SL - L.W[1]);
   T mR = R.W[0] * (SR - R.W[1]);
-  T Ss = (R.W[4] - L.W[4] + mL * L.W[1] - mR * R.W[1]) / (mL - mR);
+  T Ss = divv(R.W[4] - L.W[4] + mL * L.W[1] - mR * R.W[1], mL - mR);
   // region: SL >= 0 -> FL; S* >= 0 -> left star; SR > 0 -> right star; else FR
   const bool useL = SL >= T(0);
   const bool left = Ss >= T(0);
@@ -485,7 +494,7 @@ template <class T> __device__ __forceinline__ void hllc(const Side<T>& L, const 
   T wK = left ? L.W[3] : R.W[3];
   T rK = left ? L.W[0] : R.W[0];
   T pK = left ? L.W[4] : R.W[4];
-  T f = mK / (SK - Ss);
+  T f = divv(mK, SK - Ss);
   T Us[5], UK[5], FK[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -496,7 +505,7 @@ template <class T> __device__ __forceinline__ void hllc(const Side<T>& L, const 
   Us[1] = f * Ss;
   Us[2] = f * vK;
   Us[3] = f * wK;
-  Us[4] = f * (UK[4] / rK + (Ss - uK) * (Ss + pK / mK));
+  Us[4] = f * (divv(UK[4], rK) + (Ss - uK) * (Ss + divv(pK, mK)));
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     T Fs = FK[v] + SK * (Us[v] - UK[v]);
@@ -668,8 +677,8 @@ template <class T> __device__ __forceinline__ bool roe(const Side<T>& L, const S
   T a3 = d2 - A.v * d0;
   T a4 = d3 - A.w * d0;
   T d4b = d4 - a3 * A.v - a4 * A.w;
-  T a2 = g.gm1 / A.a2 * (d0 * (A.H - A.u * A.u) + A.u * d1 - d4b);
-  T a1 = (d0 * (A.u + a) - d1 - a * a2) / (T(2) * a);
+  T a2 = divv(g.gm1, A.a2) * (d0 * (A.H - A.u * A.u) + A.u * d1 - d4b);
+  T a1 = divv(d0 * (A.u + a) - d1 - a * a2, T(2) * a);
   T a5 = d0 - (a1 + a2);
   T K11 = A.u - a, K14 = A.H - A.u * a;
   T K51 = A.u + a, K54 = A.H + A.u * a;
@@ -677,7 +686,7 @@ template <class T> __device__ __forceinline__ bool roe(const Side<T>& L, const S
   // intermediate states U*1 = UL + a1 K1, U*2 = U*1 + a2 K2 + a3 K3 + a4 K4
   T s0 = L.U[0] + a1, s1 = L.U[1] + a1 * K11, s2 = L.U[2] + a1 * A.v, s3 = L.U[3] + a1 * A.w, s4 = L.U[4] + a1 * K14;
   if (!(s0 > T(0))) return false;
-  T p1 = g.gm1 * (s4 - T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3) / s0);
+  T p1 = g.gm1 * (s4 - divv(T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3), s0));
   if (!(p1 > T(0))) return false;
   s0 = s0 + a2;
   s1 = s1 + a2 * A.u;
@@ -685,7 +694,7 @@ template <class T> __device__ __forceinline__ bool roe(const Side<T>& L, const S
   s3 = s3 + a2 * A.w + a4;
   s4 = s4 + a2 * K24 + a3 * A.v + a4 * A.w;
   if (!(s0 > T(0))) return false;
-  T p2 = g.gm1 * (s4 - T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3) / s0);
+  T p2 = g.gm1 * (s4 - divv(T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3), s0));
   if (!(p2 > T(0))) return false;
   T c1 = absv(A.u - a) * a1;
   T c2 = absv(A.u) * a2;
@@ -791,7 +800,7 @@ template <class T> __device__ __forceinline__ void cons_local(const T W[5], int 
   if constexpr (FastRcp<T>::on)
     U[4] = W[4] * g.igm1 + T(0.5) * W[0] * ke;
   else
-    U[4] = W[4] / g.gm1 + T(0.5) * W[0] * ke;
+    U[4] = divv(W[4], g.gm1) + T(0.5) * W[0] * ke;
 }
 
 }  // namespace hyd
