@@ -184,6 +184,12 @@ template <class T> __device__ __forceinline__ T csound(T rho, T p, const Gas<T>&
 template <int LIM = -1, class T> __device__ __forceinline__ T slope(int lim, T theta, T dL, T dR) {
   if (LIM == LIM_MINMOD1) {
     T prod = dL * dR;
+    if constexpr (FastRcp<T>::on) {
+      // the same values for finite data (prod > 0 leaves dL != 0): one min
+      // and one sign copy instead of compares and selects
+      const T r = copysignf(fminf(fabsf(dL), fabsf(dR)), dL);
+      return prod > T(0) ? r : T(0);
+    }
     T a = absv(dL), b = absv(dR);
     T m = b < a ? b : a;
     T r = dL > T(0) ? m : -m;
@@ -337,8 +343,14 @@ template <class T>
 __device__ __forceinline__ void trace_plm(const T W0[5], const T dW[5], T dtdx, const Gas<T>& g, T Wl[5], T Wr[5]) {
   Eig<T> e;
   eig(W0, g, e);
-  T lamM = e.lam[4] > T(0) ? e.lam[4] : T(0);
-  T lamm = e.lam[0] < T(0) ? e.lam[0] : T(0);
+  T lamM, lamm;
+  if constexpr (FastRcp<T>::on) {
+    lamM = fmaxf(e.lam[4], 0.0f);
+    lamm = fminf(e.lam[0], 0.0f);
+  } else {
+    lamM = e.lam[4] > T(0) ? e.lam[4] : T(0);
+    lamm = e.lam[0] < T(0) ? e.lam[0] : T(0);
+  }
   T fr = T(0.5) * (T(1) - lamM * dtdx);
   T fl = T(0.5) * (T(1) + lamm * dtdx);
 #pragma unroll
@@ -370,8 +382,14 @@ __device__ __forceinline__ void trace_ppm(const T W0[5], const T WL[5], const T 
                                           T Wr[5]) {
   Eig<T> e;
   eig(W0, g, e);
-  T lamM = e.lam[4] > T(0) ? e.lam[4] : T(0);
-  T lamm = e.lam[0] < T(0) ? e.lam[0] : T(0);
+  T lamM, lamm;
+  if constexpr (FastRcp<T>::on) {
+    lamM = fmaxf(e.lam[4], 0.0f);
+    lamm = fminf(e.lam[0], 0.0f);
+  } else {
+    lamM = e.lam[4] > T(0) ? e.lam[4] : T(0);
+    lamm = e.lam[0] < T(0) ? e.lam[0] : T(0);
+  }
   T dA[5], W6[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -671,14 +689,29 @@ template <class T> __device__ __forceinline__ bool roe(const Side<T>& L, const S
   RAvg<T> A;
   ravg(L, R, g, A);
   if (!(A.a2 > T(0))) return false;
-  T a = sqrtv(A.a2);
+  // FP32: a, (gamma-1)/a^2 and 1/(2a) from one reciprocal square root
+  T a, gma2, i2a;
+  if constexpr (FastRcp<T>::on) {
+    const T ia = rsqrtf(A.a2);
+    a = A.a2 * ia;
+    gma2 = g.gm1 * (ia * ia);
+    i2a = T(0.5) * ia;
+  } else {
+    a = sqrtv(A.a2);
+  }
   T d0 = R.U[0] - L.U[0], d1 = R.U[1] - L.U[1], d2 = R.U[2] - L.U[2], d3 = R.U[3] - L.U[3],
     d4 = R.U[4] - L.U[4];
   T a3 = d2 - A.v * d0;
   T a4 = d3 - A.w * d0;
   T d4b = d4 - a3 * A.v - a4 * A.w;
-  T a2 = divv(g.gm1, A.a2) * (d0 * (A.H - A.u * A.u) + A.u * d1 - d4b);
-  T a1 = divv(d0 * (A.u + a) - d1 - a * a2, T(2) * a);
+  T a2, a1;
+  if constexpr (FastRcp<T>::on) {
+    a2 = gma2 * (d0 * (A.H - A.u * A.u) + A.u * d1 - d4b);
+    a1 = (d0 * (A.u + a) - d1 - a * a2) * i2a;
+  } else {
+    a2 = divv(g.gm1, A.a2) * (d0 * (A.H - A.u * A.u) + A.u * d1 - d4b);
+    a1 = divv(d0 * (A.u + a) - d1 - a * a2, T(2) * a);
+  }
   T a5 = d0 - (a1 + a2);
   T K11 = A.u - a, K14 = A.H - A.u * a;
   T K51 = A.u + a, K54 = A.H + A.u * a;
