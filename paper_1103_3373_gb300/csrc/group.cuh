@@ -205,7 +205,7 @@ template <class T> __device__ __forceinline__ unsigned state_status(const T Un[5
   if (!(Un[0] > T(0))) {
     st |= ST_NEG_DENS;
   } else {
-    T p = gas.gm1 * (Un[4] - T(0.5) * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) / Un[0]);
+    T p = gas.gm1 * (Un[4] - divv(T(0.5) * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]), Un[0]));
     if (!(p > T(0))) st |= ST_NEG_PRES;
   }
   return st;

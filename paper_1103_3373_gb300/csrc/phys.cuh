@@ -415,8 +415,15 @@ __device__ __forceinline__ void trace_ppm(const T W0[5], const T WL[5], const T 
     T c1 = hdt * (lref - la);
     T c2 = tdt * (lref * lref - la * la);
     T X[5];
+    if constexpr (FastRcp<T>::on) {
+      // c1 (dA -/+ W6) + c2 W6 = c1 dA + (c2 -/+ c1) W6: one coefficient per wave
+      const T k = pos ? c2 - c1 : c2 + c1;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) X[v] = c1 * (pos ? dA[v] - W6[v] : dA[v] + W6[v]) + c2 * W6[v];
+      for (int v = 0; v < 5; ++v) X[v] = fmaf(k, W6[v], c1 * dA[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) X[v] = c1 * (pos ? dA[v] - W6[v] : dA[v] + W6[v]) + c2 * W6[v];
+    }
     T coef = lproj(e, a, X);
     radd(e, a, pos ? coef : T(0), Wr);
     radd(e, a, neg ? coef : T(0), Wl);
