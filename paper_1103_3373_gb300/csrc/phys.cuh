@@ -479,6 +479,11 @@ __device__ __forceinline__ void einfeldt(const Side<T>& L, const Side<T>& R, con
   RAvg<T> A;
   ravg(L, R, g, A);
   T a = A.a2 > T(0) ? sqrtv(A.a2) : T(0);
+  if constexpr (FastRcp<T>::on) {
+    SL = fminf(L.W[1] - L.c, A.u - a);
+    SR = fmaxf(R.W[1] + R.c, A.u + a);
+    return;
+  }
   SL = L.W[1] - L.c;
   T t = A.u - a;
   if (t < SL) SL = t;
@@ -491,8 +496,14 @@ __device__ __forceinline__ void einfeldt(const Side<T>& L, const Side<T>& R, con
 template <class T> __device__ __forceinline__ void hlle(const Side<T>& L, const Side<T>& R, const Gas<T>& g, T F[5]) {
   T SL, SR;
   einfeldt(L, R, g, SL, SR);
-  T bp = SR > T(0) ? SR : T(0);
-  T bm = SL < T(0) ? SL : T(0);
+  T bp, bm;
+  if constexpr (FastRcp<T>::on) {
+    bp = fmaxf(SR, 0.0f);
+    bm = fminf(SL, 0.0f);
+  } else {
+    bp = SR > T(0) ? SR : T(0);
+    bm = SL < T(0) ? SL : T(0);
+  }
   T inv = divv(T(1), bp - bm);
 #pragma unroll
   for (int v = 0; v < 5; ++v) F[v] = (bp * L.F[v] - bm * R.F[v] + bp * bm * (R.U[v] - L.U[v])) * inv;
