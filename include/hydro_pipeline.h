@@ -74,7 +74,7 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
  *   dev_in, dev_out  device fields of the same shape (distinct);
  *   flux, dev_status optional, as hydro_advance_uniform (whole-box order);
  *   cfl      Courant number of the next dt;
- *   red_ws   hydro_cfl_workspace_bytes() of device scratch;
+ *   red_ws   hydro_pipeline_workspace_bytes(h) of device scratch;
  *   ws2      the second compute stream's scratch (hydro_workspace_bytes(p);
  *            may be NULL when that is 0).
  * Returns HYDRO_EINVAL for bad arguments (also a scheme needing more halo
@@ -84,6 +84,10 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
 int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* host_in, void* host_out,
                         double* host_dt, void* dev_in, void* dev_out, void* flux, unsigned* dev_status, double cfl,
                         void* red_ws, size_t red_ws_bytes, void* ws2, size_t ws2_bytes, void* stream);
+
+/* hydro_pipeline_workspace_bytes — device scratch hydro_pipeline_step needs
+ * as red_ws (the CFL reduction's); 0 for NULL. */
+size_t hydro_pipeline_workspace_bytes(const hydro_pipeline* h);
 
 /* hydro_pipeline_destroy — release streams, events and the object (NULL: no-op).
  * Synchronises the pipeline's own streams first. */

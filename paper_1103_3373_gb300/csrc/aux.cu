@@ -166,10 +166,11 @@ __global__ void cfl_partial_kernel(const S* __restrict__ U, int G, long long gst
   }
 }
 
-// Pass 2: one CTA reduces the partials and writes
+// Pass 2: one CTA reduces the partials of nseg pass-1 launches of n CTAs
+// each (laid out [segment][direction][CTA]) and writes
 //   smax = max_d (max speed_d) / dx_d,   dt = cfl / smax.
-__global__ void cfl_final_kernel(const double* __restrict__ part, int n, double dx0, double dx1, double dx2,
-                                 double cfl, double* dt, double* smax) {
+__global__ void cfl_final_kernel(const double* __restrict__ part, int nseg, int n, double dx0, double dx1,
+                                 double dx2, double cfl, double* dt, double* smax) {
   __shared__ double sh[32];
   __shared__ int anybad;
   __shared__ double md[3];
@@ -178,8 +179,9 @@ __global__ void cfl_final_kernel(const double* __restrict__ part, int n, double 
   for (int d = 0; d < 3; ++d) {
     double m = 0.0;
     bool bad = false;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double v = part[d * n + i];
+    for (int i = threadIdx.x; i < nseg * n; i += blockDim.x) {
+      const int s = i / n, b = i - s * n;
+      double v = part[((long long)s * 3 + d) * n + b];
       if (isnan(v)) bad = true;
       m = fmax(m, v);
     }
@@ -252,15 +254,20 @@ cudaError_t launch_gather(const void* field, int X, int Y, int Z, int bc, const 
 
 constexpr int RED_MAX_CTAS = 2048;
 
-cudaError_t launch_cfl(const void* U, int G, long long gs, long long vs, long long cells, int dbl, double gamma,
-                       double dfl, double pfl, const double* dx, double cfl, double* dt, double* smax, double* ws,
-                       cudaStream_t st, int nsm) {
-  long long total = (long long)G * cells;
-  int threads = 256;
+// CTAs of one pass-1 launch over `total` cells.
+int cfl_grid(long long total, int nsm) {
+  const int threads = 256;
   long long want = (total + threads - 1) / threads;
   int grid = (int)(want < 4LL * nsm ? want : 4LL * nsm);
   if (grid < 1) grid = 1;
   if (grid > RED_MAX_CTAS) grid = RED_MAX_CTAS;
+  return grid;
+}
+
+// Pass 1 into part[3][grid].
+cudaError_t launch_cfl_partial(const void* U, int G, long long gs, long long vs, long long cells, int dbl,
+                               double gamma, double dfl, double pfl, double* ws, int grid, cudaStream_t st) {
+  const int threads = 256;
   // 16-byte loads when every group's variables start on a 16-byte boundary
   const int w = dbl ? 2 : 4;
   const bool vec = ((uintptr_t)U % 16 == 0) && cells % w == 0 && gs % w == 0 && vs % w == 0;
@@ -279,8 +286,23 @@ cudaError_t launch_cfl(const void* U, int G, long long gs, long long vs, long lo
       cfl_partial_kernel<float, false><<<grid, threads, 0, st>>>((const float*)U, G, gs, vs, cells, gamma, dfl, pfl,
                                                                  ws);
   }
-  cfl_final_kernel<<<1, 1024, 0, st>>>(ws, grid, dx[0], dx[1], dx[2], cfl, dt, smax);
   return cudaGetLastError();
+}
+
+// Pass 2 over nseg pass-1 launches of `grid` CTAs each.
+cudaError_t launch_cfl_final(const double* ws, int nseg, int grid, const double* dx, double cfl, double* dt,
+                             double* smax, cudaStream_t st) {
+  cfl_final_kernel<<<1, 1024, 0, st>>>(ws, nseg, grid, dx[0], dx[1], dx[2], cfl, dt, smax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfl(const void* U, int G, long long gs, long long vs, long long cells, int dbl, double gamma,
+                       double dfl, double pfl, const double* dx, double cfl, double* dt, double* smax, double* ws,
+                       cudaStream_t st, int nsm) {
+  const int grid = cfl_grid((long long)G * cells, nsm);
+  cudaError_t e = launch_cfl_partial(U, G, gs, vs, cells, dbl, gamma, dfl, pfl, ws, grid, st);
+  if (e != cudaSuccess) return e;
+  return launch_cfl_final(ws, 1, grid, dx, cfl, dt, smax, st);
 }
 
 cudaError_t launch_totals(const void* U, int G, long long gs, long long vs, long long cells, int dbl, double* out,

@@ -410,7 +410,7 @@ int hydro_cfl_dt(const void* U, int G, long long group_stride, long long var_str
   if (precision < 0 || precision > 2) return HYDRO_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (!finite_pos(dx[d])) return HYDRO_EINVAL;
-  if (!workspace || workspace_bytes < (size_t)RED_MAX_CTAS * sizeof(double)) return HYDRO_EWORKSPACE;
+  if (!workspace || workspace_bytes < (size_t)3 * RED_MAX_CTAS * sizeof(double)) return HYDRO_EWORKSPACE;
   int dev;
   int rc = current_device(&dev);
   if (rc) return rc;

@@ -161,7 +161,7 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   const size_t need_ws = hydro_workspace_bytes(p, h->N);
   if (need_ws && (!p->workspace || p->workspace_bytes < need_ws || !ws2 || ws2_bytes < need_ws))
     return HYDRO_EWORKSPACE;
-  if (!red_ws || red_ws_bytes < hydro_cfl_workspace_bytes()) return HYDRO_EWORKSPACE;
+  if (!red_ws || red_ws_bytes < hydro_pipeline_workspace_bytes(h)) return HYDRO_EWORKSPACE;
   const size_t es = p->precision == HYDRO_FP64 ? sizeof(double) : sizeof(float);
   const long long XYZ = (long long)h->X * h->Y * h->Z;
   cudaStream_t user = (cudaStream_t)stream;
@@ -218,6 +218,8 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   e = cudaEventRecord(h->ev_c1, c[1]);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c[0], h->ev_c1, 0);
   if (e != cudaSuccess) return fail(h, user, hyd::record_cuda_error(e));
+  // (one reduction over the whole box: per-slab reductions interleaved with
+  // the slab kernels measured slower, their CTAs competing for the SMs)
   int rc = hydro_cfl_dt(dev_out, 1, 5 * XYZ, XYZ, XYZ, p->precision, p->gamma, p->dens_floor, p->pres_floor, p->dx,
                         cfl, const_cast<double*>(p->dt_dev), nullptr, red_ws, red_ws_bytes, c[0]);
   if (rc != HYDRO_OK) return fail(h, user, rc);
@@ -236,6 +238,8 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
   h->prev_dev_out = dev_out;
   return HYDRO_OK;
 }
+
+size_t hydro_pipeline_workspace_bytes(const hydro_pipeline* h) { return h ? hydro_cfl_workspace_bytes() : 0; }
 
 int hydro_pipeline_destroy(hydro_pipeline* h) {
   if (h) release(h);

@@ -126,6 +126,8 @@ def _lib():
         L.hydro_pipeline_step.argtypes = [vp, P, vp, vp, vp, vp, vp, vp, vp, d, vp, ctypes.c_size_t, vp,
                                           ctypes.c_size_t, vp]
         L.hydro_pipeline_destroy.argtypes = [vp]
+        L.hydro_pipeline_workspace_bytes.argtypes = [vp]
+        L.hydro_pipeline_workspace_bytes.restype = ctypes.c_size_t
         L.hydro_gather_uniform.argtypes = [vp, i, i, i, i, vp, i, i, i, i, vp, vp]
         L.hydro_cfl_workspace_bytes.argtypes = []
         L.hydro_cfl_workspace_bytes.restype = ctypes.c_size_t
@@ -254,6 +256,7 @@ class Pipeline:
         self._h = h
         self.shape = (5, Z, Y, X)
         self.nslab = n
+        self.workspace_bytes = int(_lib().hydro_pipeline_workspace_bytes(h))
 
     def step(self, params: Params, host_in, host_out, dev_in, dev_out, cfl, red_ws, host_dt=None, flux=None,
              status=None, ws2=None, stream=None):

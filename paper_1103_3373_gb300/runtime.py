@@ -130,6 +130,7 @@ class HostBoxStepper:
             [(s + 1) * GZ // slabs - s * GZ // slabs for s in range(slabs)]
         nws = H.hydro_workspace_bytes(b.p, N)
         self.ws2 = torch.empty(nws, dtype=torch.uint8, device=b.dev) if nws else None
+        self.red_ws = torch.empty(self.pipe.workspace_bytes, dtype=torch.uint8, device=b.dev)
         # three device fields in rotation (in = D[2n % 3], out = D[(2n+1) % 3]):
         # consecutive steps then chain, the copy-in of one overlapping the
         # end of the last (include/hydro_pipeline.h)
@@ -140,7 +141,7 @@ class HostBoxStepper:
         b = self.box
         d = self.dev_fields
         din, dout = d[(2 * self.n) % 3], d[(2 * self.n + 1) % 3]
-        self.pipe.step(b.p, self.host_in, self.host_out, din, dout, b.cfl, b.red_ws, host_dt=self.host_dt,
+        self.pipe.step(b.p, self.host_in, self.host_out, din, dout, b.cfl, self.red_ws, host_dt=self.host_dt,
                        flux=b.flux, status=b.status, ws2=self.ws2, stream=b.stream)
         b.a, b.b = dout, din
         self.n += 1

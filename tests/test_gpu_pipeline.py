@@ -164,6 +164,13 @@ def test_pipeline_argument_errors(torch_dev):
     with pytest.raises(H.HydroError):                    # PPM + CTU needs 3 ghost layers, planned for 2
         pipe.step(p, a, b, da, db, 0.4, ws)
     pipe.close()
+    # the per-slab CFL maxima need hydro_pipeline_workspace_bytes() of scratch
+    pipe = H.Pipeline(32, 32, 64, 3, slabs=4)
+    assert pipe.workspace_bytes >= H.hydro_cfl_workspace_bytes()
+    with pytest.raises(H.HydroError) as ei:
+        pipe.step(p, a, b, da, db, 0.4, ws[:1024])
+    assert ei.value.code == H.EWORKSPACE
+    pipe.close()
     # FP64 kernels keep their rings in scratch: the second compute stream's
     # is required, checked before any work is enqueued
     pipe = H.Pipeline(32, 32, 64, 3, slabs=2)
