@@ -234,8 +234,14 @@ __device__ __forceinline__ void ppm(T wmm, T wm, T w0, T wp, T wpp, int lim, T t
   T dm = slope<LIM>(lim, theta, wm - wmm, w0 - wm);
   T d0 = slope<LIM>(lim, theta, w0 - wm, wp - w0);
   T dp = slope<LIM>(lim, theta, wp - w0, wpp - wp);
-  T L = T(0.5) * (wm + w0) - divv(d0 - dm, T(6));
-  T R = T(0.5) * (w0 + wp) - divv(dp - d0, T(6));
+  T L, R;
+  if constexpr (FastRcp<T>::on) {
+    L = T(0.5) * (wm + w0) - (d0 - dm) * T(1.0 / 6.0);
+    R = T(0.5) * (w0 + wp) - (dp - d0) * T(1.0 / 6.0);
+  } else {
+    L = T(0.5) * (wm + w0) - divv(d0 - dm, T(6));
+    R = T(0.5) * (w0 + wp) - divv(dp - d0, T(6));
+  }
   // constraints as selects: local extremum -> flat; overshoot -> move one edge
   const bool ext = (R - w0) * (w0 - L) <= T(0);
   T dA = R - L;
@@ -737,16 +743,25 @@ template <class T> __device__ __forceinline__ bool roe(const Side<T>& L, const S
   // intermediate states U*1 = UL + a1 K1, U*2 = U*1 + a2 K2 + a3 K3 + a4 K4
   T s0 = L.U[0] + a1, s1 = L.U[1] + a1 * K11, s2 = L.U[2] + a1 * A.v, s3 = L.U[3] + a1 * A.w, s4 = L.U[4] + a1 * K14;
   if (!(s0 > T(0))) return false;
-  T p1 = g.gm1 * (s4 - divv(T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3), s0));
-  if (!(p1 > T(0))) return false;
+  if constexpr (FastRcp<T>::on) {
+    // p > 0  <=>  2 E rho > |m|^2 for rho > 0 (and gamma > 1)
+    if (!(T(2) * s4 * s0 > s1 * s1 + s2 * s2 + s3 * s3)) return false;
+  } else {
+    T p1 = g.gm1 * (s4 - divv(T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3), s0));
+    if (!(p1 > T(0))) return false;
+  }
   s0 = s0 + a2;
   s1 = s1 + a2 * A.u;
   s2 = s2 + a2 * A.v + a3;
   s3 = s3 + a2 * A.w + a4;
   s4 = s4 + a2 * K24 + a3 * A.v + a4 * A.w;
   if (!(s0 > T(0))) return false;
-  T p2 = g.gm1 * (s4 - divv(T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3), s0));
-  if (!(p2 > T(0))) return false;
+  if constexpr (FastRcp<T>::on) {
+    if (!(T(2) * s4 * s0 > s1 * s1 + s2 * s2 + s3 * s3)) return false;
+  } else {
+    T p2 = g.gm1 * (s4 - divv(T(0.5) * (s1 * s1 + s2 * s2 + s3 * s3), s0));
+    if (!(p2 > T(0))) return false;
+  }
   T c1 = absv(A.u - a) * a1;
   T c2 = absv(A.u) * a2;
   T c3 = absv(A.u) * a3;
