@@ -857,8 +857,13 @@ __device__ __forceinline__ void store_local(T* p, int s, const LocalComps& lc, c
 // result equals cons() of the rotated-back state value for value.
 template <class T> __device__ __forceinline__ void cons_local(const T W[5], int d, const Gas<T>& g, T U[5]) {
   T a = W[1] * W[1], b = W[2] * W[2], c = W[3] * W[3];
-  // global (u, v, w) = (n, t1, t2) for x, (t2, n, t1) for y, (t1, t2, n) for z
-  T ke = d == 0 ? a + b + c : (d == 1 ? c + a + b : b + c + a);
+  // global (u, v, w) = (n, t1, t2) for x, (t2, n, t1) for y, (t1, t2, n) for z;
+  // the FP32 forms take one order for every direction
+  T ke;
+  if constexpr (FastRcp<T>::on)
+    ke = a + b + c;
+  else
+    ke = d == 0 ? a + b + c : (d == 1 ? c + a + b : b + c + a);
   U[0] = W[0];
   U[1] = W[0] * W[1];
   U[2] = W[0] * W[2];
