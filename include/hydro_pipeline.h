@@ -89,6 +89,16 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
  * as red_ws (the CFL reduction's); 0 for NULL. */
 size_t hydro_pipeline_workspace_bytes(const hydro_pipeline* h);
 
+/*
+ * hydro_pipeline_plan — the copy plan hydro_pipeline_create makes, on the
+ * host only (no device call): zb[nslab+1] slab boundaries (planes) and, per
+ * slab, up to two input plane ranges chunks[s] = {lo0, hi0, lo1, hi1} (an
+ * empty range has lo = hi) whose copy completes slab s's input and halo, in
+ * copy order.  Same argument rules as hydro_pipeline_create (N need not be
+ * 16 here); HYDRO_EINVAL otherwise.
+ */
+int hydro_pipeline_plan(int Z, int N, int ghost, int bc, int nslab, const int* layers, int* zb, int* chunks);
+
 /* hydro_pipeline_destroy — release streams, events and the object (NULL: no-op).
  * Synchronises the pipeline's own streams first. */
 int hydro_pipeline_destroy(hydro_pipeline* h);

@@ -54,18 +54,46 @@ void release(hydro_pipeline* h) {
 // Input plane ranges per slab, in copy order: the ranges whose arrival
 // completes slab s's input and halo.  Periodic boxes send the last `ghost`
 // planes first (slab 0's lower halo); slab s < S-1 then needs the planes up
-// to zb[s+1] + ghost; the last slab needs the rest.
-void plan(hydro_pipeline* h) {
-  const int S = h->nslab, g = h->ghost, Z = h->Z;
-  const bool periodic = h->bc == HYDRO_BC_PERIODIC;
-  h->chunk.assign(S, {});
+// to zb[s+1] + ghost; the last slab needs the rest.  chunk[s] = {lo0, hi0,
+// lo1, hi1}: up to two ranges (the second empty: lo1 = hi1 = 0).
+void plan_ranges(int Z, int ghost, int bc, int S, const int* zb, int (*chunk)[4]) {
+  const bool periodic = bc == HYDRO_BC_PERIODIC;
   int lo = 0;
   for (int s = 0; s < S; ++s) {
-    if (s == 0 && periodic) h->chunk[s].push_back({Z - g, Z});
-    int hi = s < S - 1 ? h->zb[s + 1] + g : (periodic ? Z - g : Z);
-    h->chunk[s].push_back({lo, hi});
+    int k = 0;
+    chunk[s][0] = chunk[s][1] = chunk[s][2] = chunk[s][3] = 0;
+    if (s == 0 && periodic && ghost > 0) {
+      chunk[s][0] = Z - ghost;
+      chunk[s][1] = Z;
+      k = 2;
+    }
+    const int hi = s < S - 1 ? zb[s + 1] + ghost : (periodic ? Z - ghost : Z);
+    chunk[s][k] = lo;
+    chunk[s][k + 1] = hi;
     lo = hi;
   }
+}
+
+// Slab boundaries from the layer counts (NULL: an even split).
+int slab_bounds(int Z, int N, int nslab, const int* layers, int* zb) {
+  const int GZ = Z / N;
+  if (nslab < 1 || nslab > GZ) return HYDRO_EINVAL;
+  zb[0] = 0;
+  for (int s = 0; s < nslab; ++s) {
+    const int l = layers ? layers[s] : (s + 1) * GZ / nslab - s * GZ / nslab;
+    if (l < 1) return HYDRO_EINVAL;
+    zb[s + 1] = zb[s] + l * N;
+  }
+  return zb[nslab] == Z ? HYDRO_OK : HYDRO_EINVAL;
+}
+
+void plan(hydro_pipeline* h) {
+  std::vector<int> c(4 * h->nslab);
+  plan_ranges(h->Z, h->ghost, h->bc, h->nslab, h->zb.data(), reinterpret_cast<int(*)[4]>(c.data()));
+  h->chunk.assign(h->nslab, {});
+  for (int s = 0; s < h->nslab; ++s)
+    for (int k = 0; k < 4; k += 2)
+      if (c[4 * s + k + 1] > c[4 * s + k]) h->chunk[s].push_back({c[4 * s + k], c[4 * s + k + 1]});
 }
 
 // The five variables of planes [z0, z1) of a [5][Z][Y][X] field, as one 2-D copy.
@@ -100,20 +128,8 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
   if (X <= 0 || Y <= 0 || Z <= 0 || X % N || Y % N || Z % N) return HYDRO_EINVAL;
   if (ghost < 0 || ghost >= N) return HYDRO_EINVAL;
   if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
-  const int GZ = Z / N;
-  if (nslab < 1 || nslab > GZ) return HYDRO_EINVAL;
-  std::vector<int> lay(nslab);
-  if (layers) {
-    int sum = 0;
-    for (int s = 0; s < nslab; ++s) {
-      if (layers[s] < 1) return HYDRO_EINVAL;
-      lay[s] = layers[s];
-      sum += layers[s];
-    }
-    if (sum != GZ) return HYDRO_EINVAL;
-  } else {
-    for (int s = 0; s < nslab; ++s) lay[s] = (s + 1) * GZ / nslab - s * GZ / nslab;
-  }
+  std::vector<int> zb(nslab > 0 ? nslab + 1 : 1);
+  if (nslab < 1 || slab_bounds(Z, N, nslab, layers, zb.data()) != HYDRO_OK) return HYDRO_EINVAL;
   hydro_pipeline* h = new (std::nothrow) hydro_pipeline;
   if (!h) return HYDRO_EINVAL;
   h->X = X;
@@ -123,8 +139,7 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
   h->ghost = ghost;
   h->bc = bc;
   h->nslab = nslab;
-  h->zb.assign(nslab + 1, 0);
-  for (int s = 0; s < nslab; ++s) h->zb[s + 1] = h->zb[s] + lay[s] * N;
+  h->zb = zb;
   plan(h);
   h->ev_in.assign(nslab, nullptr);
   h->ev_comp.assign(nslab, nullptr);
@@ -240,6 +255,15 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
 }
 
 size_t hydro_pipeline_workspace_bytes(const hydro_pipeline* h) { return h ? hydro_cfl_workspace_bytes() : 0; }
+
+int hydro_pipeline_plan(int Z, int N, int ghost, int bc, int nslab, const int* layers, int* zb, int* chunks) {
+  if (!zb || !chunks || N <= 0 || Z <= 0 || Z % N || ghost < 0 || ghost >= N) return HYDRO_EINVAL;
+  if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
+  int rc = slab_bounds(Z, N, nslab, layers, zb);
+  if (rc != HYDRO_OK) return rc;
+  plan_ranges(Z, ghost, bc, nslab, zb, reinterpret_cast<int(*)[4]>(chunks));
+  return HYDRO_OK;
+}
 
 int hydro_pipeline_destroy(hydro_pipeline* h) {
   if (h) release(h);

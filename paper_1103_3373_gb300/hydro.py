@@ -128,6 +128,7 @@ def _lib():
         L.hydro_pipeline_destroy.argtypes = [vp]
         L.hydro_pipeline_workspace_bytes.argtypes = [vp]
         L.hydro_pipeline_workspace_bytes.restype = ctypes.c_size_t
+        L.hydro_pipeline_plan.argtypes = [i, i, i, i, i, vp, vp, vp]
         L.hydro_gather_uniform.argtypes = [vp, i, i, i, i, vp, i, i, i, i, vp, vp]
         L.hydro_cfl_workspace_bytes.argtypes = []
         L.hydro_cfl_workspace_bytes.restype = ctypes.c_size_t
@@ -238,6 +239,22 @@ def _host_ptr(t, name, dtype=None):
     if dtype is not None and str(t.dtype).split(".")[-1] != dtype:
         raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
     return t.data_ptr()
+
+
+def pipeline_plan(Z, ghost, bc=BC_PERIODIC, slabs=8, N=16):
+    """The copy plan of a Pipeline (host only): slab boundaries zb (planes)
+    and, per slab, the input plane ranges whose copy completes its input and
+    halo, in copy order."""
+    if isinstance(slabs, (list, tuple)):
+        n, lay = len(slabs), (ctypes.c_int * len(slabs))(*[int(a) for a in slabs])
+    else:
+        n, lay = int(slabs), None
+    zb = (ctypes.c_int * (max(n, 0) + 1))()
+    ch = (ctypes.c_int * (4 * max(n, 1)))()
+    _check(_lib().hydro_pipeline_plan(Z, N, ghost, bc, n, lay, zb, ch), "hydro_pipeline_plan")
+    chunks = [[(ch[4 * s + k], ch[4 * s + k + 1]) for k in (0, 2) if ch[4 * s + k + 1] > ch[4 * s + k]]
+              for s in range(n)]
+    return list(zb), chunks
 
 
 class Pipeline:
