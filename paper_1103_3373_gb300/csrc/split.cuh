@@ -262,12 +262,27 @@ __device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N>& C, con
   constexpr int M = N + 2 * G;
   constexpr int M2 = M * M, M3 = M * M * M;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int idx = tid; idx < M3; idx += nthr) {
-    const int z = idx / M2, r = idx - z * M2, y = r / M, x = r - y * M;
-    T U[5];
-    C.load5(x - G, y - G, z - G, U);
+  // the padded group into the ring: UB cells per thread are loaded before
+  // any of them is stored, so their global reads are in flight together
+  constexpr int UB = (sizeof(T) == 4 && !MIXED) ? 2 : 1;
+  for (int base = tid; base < M3; base += UB * nthr) {
+    T U[UB][5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) ring[v * M3 + idx] = U[v];
+    for (int u = 0; u < UB; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < M3) {
+        const int z = idx / M2, r = idx - z * M2, y = r / M, x = r - y * M;
+        C.load5(x - G, y - G, z - G, U[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < M3) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ring[v * M3 + idx] = U[u][v];
+      }
+    }
   }
   __syncthreads();
   const int first = o.split_order ? 2 : 0, last = o.split_order ? 0 : 2;
