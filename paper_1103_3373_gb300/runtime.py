@@ -91,6 +91,14 @@ class UniformBox:
         return best
 
 
+def rotation(n):
+    """Device fields (indices into three) of end-to-end step n: input
+    D[2n % 3], output D[(2n+1) % 3].  Step n+1's input is then neither of
+    step n's fields and its output is not step n's output, the condition for
+    chaining the two steps (include/hydro_pipeline.h)."""
+    return (2 * n) % 3, (2 * n + 1) % 3
+
+
 class HostBoxStepper:
     """End-to-end form of UniformBox.step for a caller that keeps its data on
     the host: each step copies the state in from pinned host memory, runs the
@@ -139,8 +147,8 @@ class HostBoxStepper:
 
     def step(self):
         b = self.box
-        d = self.dev_fields
-        din, dout = d[(2 * self.n) % 3], d[(2 * self.n + 1) % 3]
+        i, o = rotation(self.n)
+        din, dout = self.dev_fields[i], self.dev_fields[o]
         self.pipe.step(b.p, self.host_in, self.host_out, din, dout, b.cfl, self.red_ws, host_dt=self.host_dt,
                        flux=b.flux, status=b.status, ws2=self.ws2, stream=b.stream)
         b.a, b.b = dout, din

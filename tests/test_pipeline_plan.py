@@ -66,3 +66,16 @@ def test_even_split_and_errors():
             H.pipeline_plan(256, 3, **bad)
     with pytest.raises(H.HydroError):
         H.pipeline_plan(256, 16, slabs=2)  # ghost >= N
+
+
+def test_device_field_rotation_chains_every_step():
+    """The three-field rotation of HostBoxStepper meets the chaining
+    condition of hydro_pipeline_step at every step: the next input is
+    neither of the last step's fields, and the next output differs from the
+    last output (so the last output can still be copied out)."""
+    from paper_1103_3373_gb300 import runtime as RT
+    for n in range(12):
+        i0, o0 = RT.rotation(n)
+        i1, o1 = RT.rotation(n + 1)
+        assert len({i0, o0}) == 2 and len({i1, o1}) == 2
+        assert i1 not in (i0, o0) and o1 != o0
