@@ -37,7 +37,6 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s (CTU+PPM+Roe, FP32 vs FP64) and % roofline; p50/p99 step latency"
 UNIT = "cell-updates/s"
 N_BOX = 256
-FP64_NOMINAL_TFLOPS = 1.25  # the part's FP64 rate (not a measured peak)
 CFL = 0.4
 FLOORS = dict(dens_floor=1e-6, pres_floor=1e-6)
 CONFIG = {"workload": "uniform 256^3 periodic box as 4096 16^3-cell patch groups (3 ghost layers); lognormal "
@@ -49,8 +48,51 @@ CONFIG = {"workload": "uniform 256^3 periodic box as 4096 16^3-cell patch groups
 
 
 def sm_peak_fp32_tflops(nsm, sm_mhz):
-    """FP32 ALU peak: SMs x 128 FP32 lanes x 2 flop per FMA x clock."""
+    """Nominal FP32 ALU peak (context only): SMs x 128 FP32 lanes x 2 flop per
+    FMA x clock."""
     return nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def alu_peaks(H, torch, dev, local, seconds=0.8):
+    """Measured FMA rates of this GPU (include/hydro_peaks.h): FP32 scalar,
+    FP32 packed pairs and FP64, each a loop of independent FMA chains on 4
+    CTAs x 256 threads per SM, timed with CUDA events over about `seconds`
+    of launches after one warm-up launch, SM clock sampled meanwhile."""
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    ctas, threads = 4 * nsm, 256
+    out = {"ctas": ctas, "threads": threads, "chains_per_thread": 8}
+    s = torch.cuda.Stream(device=dev)
+    for name, kind, dt in (("fp32", H.PEAK_FP32, torch.float32), ("fp32x2", H.PEAK_FP32X2, torch.float32),
+                           ("fp64", H.PEAK_FP64, torch.float64)):
+        buf = torch.empty(ctas * threads, dtype=dt, device=dev)
+        iters = 4096
+        with torch.cuda.stream(s):
+            H.hydro_fma_peak(kind, ctas, threads, iters, buf, stream=s)  # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            H.hydro_fma_peak(kind, ctas, threads, iters, buf, stream=s)
+            b.record(s)
+        torch.cuda.synchronize()
+        one = a.elapsed_time(b) / 1e3
+        # about 20 ms per launch, `seconds` in all
+        iters = max(64, int(iters * 0.02 / max(one, 1e-6)))
+        reps = max(3, int(seconds / 0.02))
+        sampler = ClockSampler(local)
+        sampler.start()
+        flops = 0.0
+        with torch.cuda.stream(s):
+            H.hydro_fma_peak(kind, ctas, threads, iters, buf, stream=s)
+            a.record(s)
+            for _ in range(reps):
+                flops += H.hydro_fma_peak(kind, ctas, threads, iters, buf, stream=s)
+            b.record(s)
+        torch.cuda.synchronize()
+        clk = sampler.stop()
+        sec = a.elapsed_time(b) / 1e3
+        out[name] = {"tflops": flops / sec / 1e12, "seconds": sec, "launches": reps, "iters": iters,
+                     "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons")}
+        del buf
+    return out
 
 
 def measured_peaks():
@@ -63,7 +105,8 @@ def measured_peaks():
 
 # Sources the headline kernel (CTU, primitive reconstruction, FP32) is built
 # from; the stored DRAM-traffic figure is used only while they are unchanged.
-HEADLINE_SOURCES = ("phys.cuh", "group.cuh", "stages.cuh", "ctu.cuh", "kernels.cuh", "k_ctu_fp32.cu")
+HEADLINE_SOURCES = ("phys.cuh", "group.cuh", "stages.cuh", "ctu.cuh", "mhm.cuh", "vl.cuh", "split.cuh", "kernels.cuh",
+                    "k_ctu_fp32.cu")
 
 
 def source_hash():
@@ -303,6 +346,120 @@ def cpu_baseline(U, dx, budget_s=12.0):
             "single_core": {"value": S1 * 4096 / el1, "groups": S1, "seconds": el1}}
 
 
+SEDOV_GAMMA = 5.0 / 3.0
+SEDOV_FLOORS = dict(dens_floor=1e-12, pres_floor=1e-12)
+XI0 = 1.15
+
+
+def _sedov_params(H, prec, dx, dt_dev=None):
+    return H.Params(scheme=H.CTU, recon=H.PPM, riemann=H.RS_HLLC, limiter=H.LIM_MINMOD, precision=prec,
+                    gamma=SEDOV_GAMMA, dx=dx, dt_dev=dt_dev, **SEDOV_FLOORS)
+
+
+def _box_rel_l1(a, b):
+    a = a.reshape(5, -1)
+    b = b.reshape(5, -1)
+    out = []
+    for v in range(5):
+        den = np.abs(b[v]).sum()
+        if den < 1e-9 * np.abs(b[0]).sum():
+            den = np.abs(b[0]).sum()
+        out.append(float(np.abs(a[v] - b[v]).sum() / den))
+    return max(out)
+
+
+def sedov_long_study(n=512, sub=288, radii=(0.05, 0.10, 0.15, 0.20, 0.25), cfl=0.4):
+    """Precision study (--study sedov_long; about half an hour on one GB300,
+    not part of the default run): the Sedov-Taylor blast of the precision
+    test carried to a blast radius of 0.25 box lengths, the FP32-mixed form
+    on the whole n^3 box against the FP64 path (which equals the oracle bit
+    for bit in every parity test).
+
+    The FP64 reference runs on the central sub^3 sub-box with outflow edges.
+    While the blast stays inside it this is the same problem: outside the
+    blast the state is uniform, a uniform state is exactly steady in every
+    scheme, and an outflow edge of a uniform state is uniform.  Both sides of
+    that claim are checked at every report: the mixed run's field outside the
+    sub-box and the FP64 run's outermost layer equal the background exactly.
+    Both forms take the FP64 run's dt (CFL 0.4 on its state).  Reported at
+    Sedov-Taylor radii R = 0.05 ... 0.25 (t from R = xi0 (E t^2/rho)^(1/5),
+    xi0 = 1.15): relative L1 per variable (max over variables) of mixed vs
+    FP64 on the 64^3 cut around the centre and on the whole sub-box, the blast
+    radius from the density maximum along the six axis rays, and the largest
+    difference between those six profiles (symmetry).  One JSON line per
+    report."""
+    import torch
+    from paper_1103_3373_gb300 import hydro as H
+    from paper_1103_3373_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    dx = (1.0 / n,) * 3
+    a = n // 2 - sub // 2
+    Usub = W.sedov(n, gamma=SEDOV_GAMMA, window=sub)
+    bg = Usub[:, 0, 0, 0].copy()
+    # mixed form: the whole box
+    fm = torch.empty((5, n, n, n), dtype=torch.float32, device=dev)
+    for v in range(5):
+        fm[v].fill_(float(bg[v]))
+    fm[:, a:a + sub, a:a + sub, a:a + sub] = torch.tensor(Usub, dtype=torch.float32, device=dev)
+    gm = torch.empty_like(fm)
+    # FP64 reference: the sub-box
+    f64 = torch.tensor(Usub, dtype=torch.float64, device=dev)
+    g64 = torch.empty_like(f64)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    red_ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    p64 = _sedov_params(H, H.FP64, dx, dt)
+    ws = H.hydro_workspace_bytes(p64)
+    p64.workspace = torch.empty(max(ws, 16), dtype=torch.uint8, device=dev)
+    pm = _sedov_params(H, H.FP32_MIXED, dx, dt)
+    t_targets = [(R / XI0) ** 2.5 for R in radii]  # rho = E = 1
+    t, step, k = 0.0, 0, 0
+    rows = []
+    t0 = time.perf_counter()
+    bg64 = torch.tensor(bg, dtype=torch.float64, device=dev)
+    bg32 = torch.tensor(bg, dtype=torch.float32, device=dev)
+    while k < len(t_targets):
+        H.hydro_cfl_dt(f64, dx, cfl, dt, red_ws, gamma=SEDOV_GAMMA, precision=H.FP64, **SEDOV_FLOORS)
+        dtv = float(dt.item())
+        if t + dtv > t_targets[k]:
+            dtv = t_targets[k] - t
+            dt.fill_(dtv)
+        H.hydro_advance_uniform(p64, f64, g64, bc=H.BC_OUTFLOW)
+        H.hydro_advance_uniform(pm, fm, gm, bc=H.BC_OUTFLOW)
+        f64, g64 = g64, f64
+        fm, gm = gm, fm
+        t += dtv
+        step += 1
+        if t >= t_targets[k] * (1 - 1e-12):
+            torch.cuda.synchronize()
+            ref = f64.cpu().numpy()
+            got = fm[:, a:a + sub, a:a + sub, a:a + sub].double().cpu().numpy()
+            c = sub // 2
+            cut = (slice(None), slice(c - 32, c + 32), slice(c - 32, c + 32), slice(c - 32, c + 32))
+            # outside the sub-box the mixed run is still the background
+            out_dev = float((fm[:, :a].reshape(5, -1) - bg32[:, None]).abs().max())
+            edge = torch.cat([f64[:, 0].reshape(5, -1), f64[:, -1].reshape(5, -1), f64[:, :, 0].reshape(5, -1),
+                              f64[:, :, -1].reshape(5, -1), f64[:, :, :, 0].reshape(5, -1),
+                              f64[:, :, :, -1].reshape(5, -1)], dim=1)
+            edge_dev = float((edge - bg64[:, None]).abs().max())
+            rho = ref[0]
+            rays = [rho[c, c, c:], rho[c, c, :c][::-1], rho[c, c:, c], rho[c, :c, c][::-1], rho[c:, c, c],
+                    rho[:c, c, c][::-1]]
+            rays = [r[:min(len(x) for x in rays)] for r in rays]
+            R_num = (np.mean([np.argmax(r) for r in rays]) + 0.5) / n
+            sym = float(max(np.abs(r - rays[0]).max() for r in rays[1:]))
+            row = {"R_target": radii[k], "t": t, "steps": step, "R_numeric": R_num,
+                   "R_sedov_taylor": XI0 * t ** 0.4,
+                   "rel_l1_cut64": _box_rel_l1(got[cut], ref[cut]), "rel_l1_subbox": _box_rel_l1(got, ref),
+                   "max_rel_dev_density_cut": float(np.abs(got[0][cut[1:]] - ref[0][cut[1:]]).max() /
+                                                   np.abs(ref[0][cut[1:]]).max()),
+                   "mixed_outside_subbox_max_dev": out_dev, "fp64_subbox_edge_max_dev": edge_dev,
+                   "ray_symmetry_max_diff_fp64": sym, "wall_s": time.perf_counter() - t0}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            k += 1
+    return rows
+
+
 def reference_arm(args, rank, world):
     """--impl reference: the oracle (FP64 CPU), as it stands, on the host cores."""
     if rank != 0:
@@ -368,6 +525,9 @@ def main():
     ap.add_argument("--legs", default="all",
                     help="comma list of extra legs to run: precisions, schemes, amr_levels, amr_hierarchy, "
                          "serving (default all)")
+    ap.add_argument("--study", default="", choices=["", "sedov_long"],
+                    help="run only this long study instead of the benchmark (sedov_long: the Sedov blast to "
+                         "R = 0.25, mixed vs FP64, about half an hour)")
     ap.add_argument("--block-threads", type=int, default=0,
                     help="use this many threads per CTA (capped per kernel) instead of autotuning")
     args = ap.parse_args()
@@ -377,6 +537,11 @@ def main():
     rank, world, local = replicas.rank_info()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.study == "sedov_long":
+        from paper_1103_3373_gb300 import build as hb
+        hb.build()
+        sedov_long_study()
+        return 0
 
     import torch
     from paper_1103_3373_gb300 import build as hb
@@ -417,13 +582,18 @@ def main():
     st = box.status.cpu().numpy()
     finite = bool(torch.isfinite(box.state()).all().item())
 
-    # roofline of the dominant kernel (the fused CTU group update)
+    # roofline of the dominant kernel (the fused CTU group update), against
+    # the FP32 FMA rate measured on this GPU (include/hydro_peaks.h): the
+    # larger of the scalar and packed-pair forms
     with open(os.path.join(ROOT, "paper_1103_3373_gb300", "data", "flops_per_cell.json")) as fh:
         flops_cell = json.load(fh)["entries"]["ctu-ppm-roe"]["flops"]
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = sm_peak_fp32_tflops(props.multi_processor_count, sm_max)
+    alu = alu_peaks(H, torch, dev, local)
+    fp32_form = "fp32x2" if alu["fp32x2"]["tflops"] > alu["fp32"]["tflops"] else "fp32"
+    peak = alu[fp32_form]["tflops"]
+    peak_fp64 = alu["fp64"]["tflops"]
     achieved = flops_cell * cells / (adv_ms / 1e3) / 1e12
     traffic = None
     tpath = os.path.join(ROOT, "paper_1103_3373_gb300", "data", "ncu_traffic.json")
@@ -435,8 +605,11 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "advance_kernel<CTU,PPM,ROE,FP32,16> (fused gather)",
                 "flops_per_cell": flops_cell, "kernel_ms": adv_ms,
-                "peak_note": "derived, not measured: %d SMs x 128 FP32 lanes x 2 flop/FMA x %.0f MHz"
-                             % (props.multi_processor_count, sm_max),
+                "peak_note": "measured on this GPU: FP32 FMA loop (%s form, %.0f MHz median SM clock), "
+                             "include/hydro_peaks.h; nominal %d SMs x 128 lanes x 2 x %.0f MHz = %.1f"
+                             % (fp32_form, alu[fp32_form]["sm_mhz"] or 0, props.multi_processor_count, sm_max,
+                                sm_peak_fp32_tflops(props.multi_processor_count, sm_max)),
+                "alu_peaks": alu,
                 "hbm_frac_of_measured": (40.0 * cells + 30.0 * 4 * 256 * 4096) / (adv_ms / 1e3) / 1e9 /
                                         peaks.get("hbm_gbs", 6775.3)}
 
@@ -489,8 +662,8 @@ def main():
             return {"flops_per_cell": flops_tab[key]["flops"], "achieved_tflops": a, "peak_tflops": pk,
                     "frac": a / pk, "peak_note": note}
 
-        fp32_note = "derived FP32 ALU peak (as the main line)"
-        for name, prec, k in (("fp64", H.FP64, 4), ("mixed", H.FP32_MIXED, 50)) if "precisions" in legs else ():
+        fp32_note = "measured FP32 FMA rate (as the main line)"
+        for name, prec, k in (("fp64", H.FP64, 16), ("mixed", H.FP32_MIXED, 50)) if "precisions" in legs else ():
             bx = RT.UniformBox(U, make_params(H, prec, dx), cfl=CFL, device=dev, stream=stream)
             tb = bx.tune() if prec != H.FP64 else None
             bx.compute_dt()
@@ -498,8 +671,8 @@ def main():
             extra[name] = {"value": cells * k / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / k,
                            "kernel_ms": am, "steps": k,
                            "block_threads": tb["block_threads"] if tb else bx.p.block_threads,
-                           "roofline": leg_roofline("ctu-ppm-roe", am, FP64_NOMINAL_TFLOPS if prec == H.FP64 else peak,
-                                                    "nominal FP64 rate of the part, not measured" if prec == H.FP64
+                           "roofline": leg_roofline("ctu-ppm-roe", am, peak_fp64 if prec == H.FP64 else peak,
+                                                    "measured FP64 FMA rate of this GPU" if prec == H.FP64
                                                     else fp32_note)}
             del bx
             torch.cuda.empty_cache()
@@ -544,6 +717,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(CONFIG, parallelism="replicas%d" % world if world > 1 else "single GPU"),
                 "p50_step_ms": RT.percentile(step_ms, 50), "p99_step_ms": RT.percentile(step_ms, 99),
+                "step_latency_samples": len(step_ms),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 3 * args.steps,
                 "autotuned": {"block_threads": tuned["block_threads"], "grid_ctas": tuned["grid_ctas"]},

@@ -265,10 +265,14 @@ int hydro_conserved_totals(const void* U, int G, long long group_stride, long lo
  * 512^3 box fits); larger inputs return HYDRO_ETOOBIG before anything is
  * launched.
  *   Arguments, result and numerics are those of hydro_cfl_dt (dt_dev and
- *   smax_dev are device outputs the caller provides); no workspace argument.
+ *   smax_dev are device outputs the caller provides), including empty
+ *   inputs (G == 0 or cells == 0 give dt = +inf); no workspace argument.
  *   The first call on a device looks up the array's device address (with
  *   that device current) and caches it: make that first call before any
- *   stream capture.  Every call shares the one array and leaves its partials
+ *   stream capture.  The cached address belongs to the device's primary
+ *   context and is assumed to live as long as the process: after a
+ *   cudaDeviceReset the cache is stale, so do not reset a device that this
+ *   entry point has used.  Every call shares the one array and leaves its partials
  *   in it; nothing in it needs to start at zero (each call writes every
  *   partial it reads).  Calls that overlap on the GPU (different streams or
  *   host threads at once) race on the array: serialise them.

@@ -23,6 +23,10 @@
 #include "../../include/hydro.h"
 #include "phys.cuh"
 
+namespace hyd {
+int record_cuda_error(cudaError_t e);  // hydro_api.cu: keeps the text for hydro_last_cuda_error
+}
+
 namespace {
 
 constexpr int NOALLOC_MAX_PARTIALS = HYDRO_NOALLOC_MAX_PARTIALS;
@@ -130,15 +134,20 @@ __global__ void __launch_bounds__(1024) noalloc_cfl_final(const double* __restri
 }
 
 // Device address of the static partials for the current device (looked up
-// once per device, with that device current).
+// once per device, with that device current).  The cached address belongs
+// to the device's primary context: it stays valid as long as that context
+// lives, i.e. until the process exits unless the caller resets the device.
 int partials_for_current_device(double** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEV) return HYDRO_ECUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return hyd::record_cuda_error(e);
+  if (dev < 0 || dev >= NOALLOC_MAX_DEV) return hyd::record_cuda_error(cudaErrorInvalidDevice);
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_partials_ptr[dev]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess || !p) return HYDRO_ECUDA;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return hyd::record_cuda_error(e);
+    if (!p) return hyd::record_cuda_error(cudaErrorInvalidSymbol);
     g_partials_ptr[dev] = (double*)p;
   }
   *out = g_partials_ptr[dev];
@@ -153,17 +162,20 @@ extern "C" int hydro_cfl_dt_noalloc(const void* U, int G, long long group_stride
                                     long long cells, int precision, double gamma, double dens_floor,
                                     double pres_floor, const double* dx, double cfl, double* dt_dev,
                                     double* smax_dev, void* stream) {
-  if (!U || G < 0 || cells <= 0 || !dx || !dt_dev || !(gamma > 1.0) || !(cfl > 0.0)) return HYDRO_EINVAL;
+  if (!U || G < 0 || cells < 0 || !dx || !dt_dev || !(gamma > 1.0) || !(cfl > 0.0)) return HYDRO_EINVAL;
   if (precision < 0 || precision > 2) return HYDRO_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (!pos_finite(dx[d])) return HYDRO_EINVAL;
-  if (G == 0) return HYDRO_EINVAL;
   const long long total = (long long)G * cells;
-  if (total / G != cells || total > (long long)(NOALLOC_MAX_PARTIALS / 3) * NOALLOC_CELLS_PER_CTA) return HYDRO_ETOOBIG;
+  if ((G > 0 && total / G != cells) || total > (long long)(NOALLOC_MAX_PARTIALS / 3) * NOALLOC_CELLS_PER_CTA)
+    return HYDRO_ETOOBIG;
   double* part = nullptr;
   int rc = partials_for_current_device(&part);
   if (rc != HYDRO_OK) return rc;
-  const int nblk = (int)((total + NOALLOC_CELLS_PER_CTA - 1) / NOALLOC_CELLS_PER_CTA);
+  // no cells (G == 0 or cells == 0): one CTA writes zero maxima and dt is
+  // cfl / 0 = inf, as hydro_cfl_dt gives
+  int nblk = (int)((total + NOALLOC_CELLS_PER_CTA - 1) / NOALLOC_CELLS_PER_CTA);
+  if (nblk < 1) nblk = 1;
   cudaStream_t st = (cudaStream_t)stream;
   if (precision == HYDRO_FP64)
     noalloc_cfl_partial<double><<<nblk, NOALLOC_THREADS, 0, st>>>((const double*)U, G, group_stride, var_stride,
@@ -172,5 +184,6 @@ extern "C" int hydro_cfl_dt_noalloc(const void* U, int G, long long group_stride
     noalloc_cfl_partial<float><<<nblk, NOALLOC_THREADS, 0, st>>>((const float*)U, G, group_stride, var_stride,
                                                                  cells, gamma, dens_floor, pres_floor, part);
   noalloc_cfl_final<<<1, 1024, 0, st>>>(part, nblk, dx[0], dx[1], dx[2], cfl, dt_dev, smax_dev);
-  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HYDRO_OK : hyd::record_cuda_error(e);
 }

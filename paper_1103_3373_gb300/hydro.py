@@ -142,6 +142,7 @@ def _lib():
         L.hydro_amr_prepare.argtypes = [A, A, vp, d, i, i, i, i, vp, vp, vp]
         L.hydro_amr_reflux.argtypes = [A, vp, A, vp, vp, d, ctypes.POINTER(ctypes.c_double), i, i, i, vp, vp]
         L.hydro_amr_restrict.argtypes = [A, A, i, i, vp, vp]
+        L.hydro_fma_peak.argtypes = [i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_double)]
         L.hydro_strerror.argtypes = [i]
         L.hydro_strerror.restype = ctypes.c_char_p
         L.hydro_last_cuda_error.argtypes = []
@@ -399,6 +400,24 @@ def hydro_cfl_dt_noalloc(U, dx, cfl, dt_out, gamma=1.4, dens_floor=0.0, pres_flo
                                      dxa, float(cfl), _ptr(dt_out, "dt_out", "float64"),
                                      _ptr(smax_out, "smax_out", "float64"), _stream(stream))
     _check(rc, "hydro_cfl_dt_noalloc")
+
+
+# ---------------------------------------------------------------- peaks (include/hydro_peaks.h)
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64 = 0, 1, 2
+
+
+def hydro_fma_peak(kind, ctas, threads, iters, out, stream=None):
+    """Enqueue one FMA-loop launch; returns its exact flop count (the caller
+    times it).  `out` holds ctas * threads floats (doubles for PEAK_FP64)."""
+    fl = ctypes.c_double(0.0)
+    n = ctas * threads
+    if out.numel() < n:
+        raise ValueError("out must hold ctas * threads elements")
+    rc = _lib().hydro_fma_peak(int(kind), int(ctas), int(threads), int(iters),
+                               _ptr(out, "out", "float64" if kind == PEAK_FP64 else "float32"), _stream(stream),
+                               ctypes.byref(fl))
+    _check(rc, "hydro_fma_peak")
+    return fl.value
 
 
 # ---------------------------------------------------------------- AMR (include/hydro_amr.h)

@@ -84,3 +84,19 @@ def test_binding_marshals_its_structs():
     a = H._CAmrLevel(1, 2, 3, 4, 5, 6, 7)
     assert (a.G, a.X, a.Y, a.Z) == (4, 5, 6, 7)
     assert [f[0] for f in H._CAmrLevel._fields_] == ["U", "origin", "map", "G", "X", "Y", "Z"]
+
+
+def test_python_constants_match_the_header():
+    """Sizes the binding copies from include/hydro.h (the no-allocation
+    entry point's scratch limit, the level-table size) are the header's."""
+    from paper_1103_3373_gb300 import hydro as H
+    src = open(os.path.join(ROOT, "include", "hydro.h")).read()
+    macro = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(HYDRO_\w+)\s+\(?(-?\d+)u?\)?", src)}
+    assert macro["HYDRO_NOALLOC_MAX_PARTIALS"] == H.NOALLOC_MAX_PARTIALS
+    assert macro["HYDRO_NOALLOC_CELLS_PER_CTA"] == H.NOALLOC_CELLS_PER_CTA
+    assert H.NOALLOC_MAX_CELLS == (macro["HYDRO_NOALLOC_MAX_PARTIALS"] // 3) * macro["HYDRO_NOALLOC_CELLS_PER_CTA"]
+    assert macro["HYDRO_MAX_LEVELS"] == H.MAX_LEVELS
+    for name in ("ETOOBIG", "EINVAL", "EGHOST", "EUNSUPPORTED", "ECUDA", "EWORKSPACE"):
+        assert macro["HYDRO_" + name] == getattr(H, name), name
+    for name in ("ST_ROE_FALLBACK", "ST_NEG_DENS", "ST_NEG_PRES", "ST_NAN", "ST_EXACT_FAIL"):
+        assert macro["HYDRO_" + name] == getattr(H, name), name

@@ -21,7 +21,7 @@ from oracle import amr as A
 from paper_1103_3373_gb300 import hydro as H
 from paper_1103_3373_gb300 import runtime as RT
 from paper_1103_3373_gb300 import workloads as W
-from tests.gpu_common import TOL_FP32, TOL_FP64, params_pair, quantise, rel_l1, tdtype
+from tests.gpu_common import assert_close, params_pair, quantise, tdtype
 
 pytestmark = pytest.mark.gpu
 N = 16
@@ -147,14 +147,13 @@ def test_hierarchy_steps_match_oracle(case, prec):
     dt0 = 0.3 * levels[0]["dx"][0] / 3.0
     hier = RT.AmrHierarchy(levels, ph)
     ref_levels = [dict(lv) for lv in levels]
-    tol = TOL_FP64 if prec == H.FP64 else TOL_FP32
     for step in range(2):
         ref = A.amr_step(ref_levels, po, dt0)
         hier.step(dt0)
         torch.cuda.synchronize()
         for l in range(len(levels)):
             got = hier.cur[l].double().cpu().numpy()
-            assert rel_l1(got, ref[l]) <= tol, (step, l, rel_l1(got, ref[l]))
+            assert_close(got, ref[l], prec, "level %d step %d" % (l, step))
             if prec == H.FP64:
                 np.testing.assert_array_equal(got, ref[l])
         # the next oracle step starts from the GPU's state (FP32: the stored values)
@@ -225,5 +224,5 @@ def test_hierarchy_step_split_scheme_outflow(scheme, prec):
         if prec == H.FP64:
             np.testing.assert_array_equal(got, ref[l])
         else:
-            assert rel_l1(got, ref[l]) <= TOL_FP32
+            assert_close(got, ref[l], prec, "level %d" % l)
     assert hier.errors() == 0

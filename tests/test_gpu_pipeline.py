@@ -19,7 +19,7 @@ import oracle as O
 from paper_1103_3373_gb300 import hydro as H
 from paper_1103_3373_gb300 import runtime as RT
 from paper_1103_3373_gb300 import workloads as W
-from tests.gpu_common import TOL_FP32, TOL_FP64, params_pair, quantise, rel_l1, tdtype, with_workspace
+from tests.gpu_common import assert_close, params_pair, quantise, tdtype, with_workspace
 
 pytestmark = pytest.mark.gpu
 
@@ -85,9 +85,8 @@ def test_zrange_slabs_equal_whole_box_and_oracle(torch_dev, prec, bc, scheme, re
     sel = (org[:, 2] >= 16) & (org[:, 2] < 64)
     Uo, Fo, So = O.advance(po, O.gather(U, org[sel], N, g, bc=bc), N)
     got = part.double().cpu().numpy()
-    tol = TOL_FP64 if prec == H.FP64 else TOL_FP32
     mine = np.stack([got[:, o[2]:o[2] + N, o[1]:o[1] + N, o[0]:o[0] + N] for o in org[sel]])
-    assert rel_l1(mine, Uo) <= tol
+    assert_close(mine, Uo, prec, "state")
     if prec == H.FP64:
         np.testing.assert_array_equal(st2.cpu().numpy()[sel], So)
 

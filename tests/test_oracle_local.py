@@ -162,6 +162,105 @@ def test_trace_single_wave_transport():
         np.testing.assert_allclose(Wr, W0 + 0.5 * (1 - lam[k].real * dtdx) * dW, rtol=1e-12, atol=1e-15)
 
 
+def _ppm_edges_along(W0, rk, alpha, beta):
+    """Edge values WL, WR of a parabola whose jump dA = WR - WL and curvature
+    W6 = 6 (W0 - (WL + WR) / 2) are alpha r and beta r (one right eigenvector)."""
+    dA = alpha * rk
+    W6 = beta * rk
+    WR = W0 - W6 / 6.0 + 0.5 * dA
+    WL = W0 - W6 / 6.0 - 0.5 * dA
+    return WL, WR, dA, W6
+
+
+def _ppm_avg_right(WR, dA, W6, s):
+    """Mean of the CW84 parabola over its last fraction s of the cell (a wave
+    of Courant number s > 0 reaching the right edge), integrated by hand:
+    WR - (s/2) (dA - (1 - 2s/3) W6)."""
+    return WR - 0.5 * s * (dA - (1.0 - 2.0 * s / 3.0) * W6)
+
+
+def _ppm_avg_left(WL, dA, W6, s):
+    """Mean over the first fraction |s| of the cell (s < 0, a wave reaching
+    the left edge): WL - (s/2) (dA + (1 + 2s/3) W6)."""
+    return WL - 0.5 * s * (dA + (1.0 + 2.0 * s / 3.0) * W6)
+
+
+def test_ppm_parabola_average_by_quadrature():
+    # the two closed forms above against a numerical average of the parabola
+    # w(xi) = WL + xi (dA + W6 (1 - xi)), xi in [0, 1]
+    WL, dA, W6 = 0.3, 0.7, -0.4
+    WR = WL + dA
+    xi = (np.arange(200000) + 0.5) / 200000
+    for s in (0.1, 0.37, 0.8):
+        seg = 1.0 - s + s * xi
+        num = np.mean(WL + seg * (dA + W6 * (1 - seg)))
+        assert _ppm_avg_right(WR, dA, W6, s) == pytest.approx(num, rel=1e-9)
+        seg = s * xi
+        num = np.mean(WL + seg * (dA + W6 * (1 - seg)))
+        assert _ppm_avg_left(WL, dA, W6, -s) == pytest.approx(num, rel=1e-9)
+
+
+@pytest.mark.parametrize("u", [0.3, -0.3, 0.0])
+def test_trace_ppm_single_wave_subsonic_mixed_signs(u):
+    """CTU step (1) with PPM for a subsonic cell (waves of both signs): a
+    parabola lying along one right eigenvector of numpy's primitive Jacobian
+    is a single wave.  At the edge the wave travels to, the traced state is
+    that wave's domain-of-dependence average of the parabola (its own speed,
+    not the fastest one); at the other edge the wave enters only through the
+    reference state, the average over the fastest wave towards that edge
+    (lambda_M = max(u + c, 0), lambda_m = min(u - c, 0))."""
+    g = 1.4
+    W0 = np.array([1.2, u, -0.15, 0.25, 1.0])  # c = 1.08 > |u|
+    A = prim_jacobian(W0, g)
+    lam, R = np.linalg.eig(A)
+    lam = lam.real
+    R = R.real
+    c = np.sqrt(g * W0[4] / W0[0])
+    dtdx = 0.35
+    sM = max(u + c, 0.0) * dtdx
+    sm = min(u - c, 0.0) * dtdx
+    assert sm < 0 < sM
+    for k in range(5):
+        for alpha, beta in ((0.02, 0.0), (0.0, 0.03), (0.015, -0.025)):
+            WL, WR, dA, W6 = _ppm_edges_along(W0, R[:, k], alpha, beta)
+            Wl, Wr = O.trace(O.PPM, W0, WL, WR, dtdx, g)
+            s = lam[k] * dtdx
+            if lam[k] > 0:
+                want_r = _ppm_avg_right(WR, dA, W6, s)
+                want_l = _ppm_avg_left(WL, dA, W6, sm)
+            elif lam[k] < 0:
+                want_r = _ppm_avg_right(WR, dA, W6, sM)
+                want_l = _ppm_avg_left(WL, dA, W6, s)
+            else:
+                # a wave at rest reaches neither edge: both edges keep the
+                # reference states
+                want_r = _ppm_avg_right(WR, dA, W6, sM)
+                want_l = _ppm_avg_left(WL, dA, W6, sm)
+            np.testing.assert_allclose(Wr, want_r, rtol=1e-12, atol=1e-15)
+            np.testing.assert_allclose(Wl, want_l, rtol=1e-12, atol=1e-15)
+
+
+def test_trace_ppm_superposition_of_waves():
+    # the tracing is linear in (dA, W6) for frozen eigenvectors: two waves of
+    # opposite signs together equal the sum of their separate corrections
+    g = 1.4
+    W0 = np.array([0.9, 0.2, 0.1, -0.3, 0.8])
+    A = prim_jacobian(W0, g)
+    lam, R = np.linalg.eig(A)
+    i_neg, i_pos = int(np.argmin(lam.real)), int(np.argmax(lam.real))
+    dtdx = 0.3
+    parts = []
+    for k, al, be in ((i_neg, 0.02, -0.01), (i_pos, -0.01, 0.03)):
+        WL, WR, _, _ = _ppm_edges_along(W0, R[:, k].real, al, be)
+        Wl, Wr = O.trace(O.PPM, W0, WL, WR, dtdx, g)
+        parts.append((Wl - WL, Wr - WR, WL - W0, WR - W0))
+    WL = W0 + parts[0][2] + parts[1][2]
+    WR = W0 + parts[0][3] + parts[1][3]
+    Wl, Wr = O.trace(O.PPM, W0, WL, WR, dtdx, g)
+    np.testing.assert_allclose(Wl - WL, parts[0][0] + parts[1][0], rtol=1e-10, atol=1e-15)
+    np.testing.assert_allclose(Wr - WR, parts[0][1] + parts[1][1], rtol=1e-10, atol=1e-15)
+
+
 # ------------------------------------------------------------------ Riemann
 def prim2cons(W, g):
     r, u, v, w, p = W

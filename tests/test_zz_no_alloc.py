@@ -67,3 +67,24 @@ def test_noalloc_grouped_layout_and_size_limit():
     assert rc == H.ETOOBIG
     torch.cuda.synchronize()
     assert dt.item() == ref_dt.item()
+
+
+def test_noalloc_empty_input_like_workspace_version():
+    """No cells (G == 0, or cells == 0): both entry points accept it and give
+    dt = cfl / 0 = +inf."""
+    import torch
+    dev = torch.device("cuda:0")
+    L = H.library()
+    Ut = torch.ones((1, 5, 16, 16, 16), dtype=torch.float32, device=dev)  # a valid pointer, never read
+    ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    dxa = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    s = torch.cuda.current_stream().cuda_stream
+    for G, cells in ((0, 4096), (1, 0)):
+        a = torch.zeros(1, dtype=torch.float64, device=dev)
+        b = torch.zeros(1, dtype=torch.float64, device=dev)
+        assert L.hydro_cfl_dt(Ut.data_ptr(), G, 5 * 4096, 4096, cells, H.FP32, 1.4, 0.0, 0.0, dxa, 0.4,
+                              a.data_ptr(), None, ws.data_ptr(), ws.numel(), s) == 0
+        assert L.hydro_cfl_dt_noalloc(Ut.data_ptr(), G, 5 * 4096, 4096, cells, H.FP32, 1.4, 0.0, 0.0, dxa, 0.4,
+                                      b.data_ptr(), None, s) == 0
+        torch.cuda.synchronize()
+        assert a.item() == float("inf") and b.item() == float("inf")
