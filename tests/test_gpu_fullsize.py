@@ -31,9 +31,10 @@ C2_IDS = ["ctu_ppm_roe", "vl_plm_hllc"]
 
 # Relative L1 per variable after N steps of the 256^3 box, FP32 / mixed
 # against FP64 (both from the same FP32-rounded initial state, each with its
-# own CFL dt).  Set from the first measurement with a margin of about 3, then
-# frozen.
-L1_AFTER_STEPS = {1: 1e-6, 5: 3e-6, 10: 6e-6, 20: 1.2e-5}
+# own CFL dt).  Set from the first measurement (CTU+PPM+Roe 3.2e-8, 6.5e-8,
+# 9.5e-8, 1.4e-7; VL+PLM+HLLC 3.1e-8, 6.0e-8, 8.0e-8, 1.05e-7) with a margin
+# of about 3, then frozen.
+L1_AFTER_STEPS = {1: 1e-7, 5: 2e-7, 10: 3e-7, 20: 4.5e-7}
 
 
 @pytest.fixture(scope="module")
