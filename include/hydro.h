@@ -251,6 +251,40 @@ int hydro_conserved_totals(const void* U, int G, long long group_stride, long lo
                            int precision, double* totals_dev, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * hydro_cfl_dt_boxes — the CFL time step (Sec. 4.3) of many independent
+ * boxes (or AMR levels) in one pass: three launches whatever the number of
+ * boxes, instead of two per box.  Box b is laid out as for hydro_cfl_dt (G
+ * groups of 5 variables: U + g*group_stride + v*var_stride + i, i < cells;
+ * a uniform field is G = 1, var_stride = cells = X*Y*Z) in `precision`'s
+ * storage type, and gets its own dt in dt_dev (device double; max speed /
+ * dx in smax_dev if not NULL).  Each box's dt equals hydro_cfl_dt's on the
+ * same data bit for bit.
+ *   dt_min_dev  (device double, may be NULL) min over boxes of
+ *               dt_scale * dt_b, NaN if any dt_b is NaN: with dt_scale = 2^l
+ *               for level l of an AMR hierarchy stepped with dt_l = dt_0 /
+ *               2^l, the largest dt_0 that satisfies every level.
+ *   workspace   device scratch of hydro_cfl_boxes_workspace_bytes() bytes.
+ * 1 <= nbox <= HYDRO_CFL_MAX_BOXES (call again for more).  Returns
+ * HYDRO_OK, HYDRO_EINVAL (null pointer, nbox out of range, G or cells < 0,
+ * dx or dt_scale not positive and finite, gamma <= 1, cfl <= 0),
+ * HYDRO_EWORKSPACE, or HYDRO_ECUDA.  Allocates nothing.
+ */
+#define HYDRO_CFL_MAX_BOXES 256
+typedef struct hydro_cfl_box {
+  const void* U;
+  int G;
+  long long group_stride, var_stride, cells;
+  double dx[3];
+  double* dt_dev;
+  double* smax_dev;
+  double dt_scale;
+} hydro_cfl_box;
+size_t hydro_cfl_boxes_workspace_bytes(void);
+int hydro_cfl_dt_boxes(const hydro_cfl_box* boxes, int nbox, int precision, double gamma, double dens_floor,
+                       double pres_floor, double cfl, double* dt_min_dev, void* workspace, size_t workspace_bytes,
+                       void* stream);
+
+/*
  * hydro_cfl_dt_noalloc — hydro_cfl_dt for callers that cannot allocate device
  * memory.  The paper has no counterpart: it serves code that runs where no
  * allocator is reachable, e.g. a plug-in enqueued inside another framework's

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/hydro.h"
 #include "phys.cuh"
 
 namespace hyd {
@@ -203,6 +204,130 @@ __global__ void cfl_final_kernel(const double* __restrict__ part, int nseg, int 
   }
 }
 
+// ---- CFL time step of many boxes in one pass (continuous batching, AMR
+// levels): the table of boxes is a kernel argument; box b owns the pass-1
+// CTAs [first_b, first_b + nblk_b), each reducing one contiguous chunk of the
+// box's G * cells cells exactly as cfl_partial_kernel does; pass 2 runs one
+// CTA per box; an optional pass 3 takes min_b scale_b dt_b.  A box's dt
+// equals hydro_cfl_dt's on the same data bit for bit: both are maxima of the
+// same per-cell FP64 values, divided and inverted the same way.
+struct CflBoxDev {
+  const void* U;
+  long long gstride, vstride, cells;
+  int G, first, nblk, pad;
+  double dx[3];
+  double* dt;
+  double* smax;
+  double scale;
+};
+constexpr int CFL_MAX_BOXES = HYDRO_CFL_MAX_BOXES;
+struct CflBoxTable {
+  int n, total;
+  CflBoxDev box[CFL_MAX_BOXES];
+};
+
+template <class S>
+__global__ void __launch_bounds__(256) cfl_boxes_partial_kernel(const __grid_constant__ CflBoxTable tab, double gamma,
+                                                                double dfloor, double pfloor,
+                                                                double* __restrict__ part) {
+  __shared__ double sh[32];
+  __shared__ int anybad;
+  // the box of this CTA: the last one whose first CTA is <= blockIdx.x
+  int lo = 0, hi = tab.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab.box[mid].first <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const CflBoxDev& bx = tab.box[lo];
+  const S* U = (const S*)bx.U;
+  const long long total = (long long)bx.G * bx.cells;
+  const int k = blockIdx.x - bx.first;
+  const long long chunk = (total + bx.nblk - 1) / bx.nblk;
+  const long long begin = (long long)k * chunk;
+  const long long end = begin + chunk < total ? begin + chunk : total;
+  if (threadIdx.x == 0) anybad = 0;
+  S m[3] = {S(0), S(0), S(0)};
+  bool bad = false;
+  Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor, (S)(1.0 / (gamma - 1.0))};
+  for (long long e = begin + threadIdx.x; e < end; e += blockDim.x) {
+    const long long gi = e / bx.cells, i = e - gi * bx.cells;
+    const S* b = U + gi * bx.gstride + i;
+    S u[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = b[v * bx.vstride];
+    fold_speed(u, gas, m, bad);
+  }
+  __syncthreads();
+  if (bad) anybad = 1;
+  for (int d = 0; d < 3; ++d) {
+    double r = block_max((double)m[d], sh);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      part[(long long)d * tab.total + blockIdx.x] = anybad ? __longlong_as_double(0x7ff8000000000000LL) : r;
+  }
+}
+
+// One CTA per box: dt_b = cfl / max_d (max speed_d / dx_d); sdt[b] = scale_b dt_b.
+__global__ void __launch_bounds__(256) cfl_boxes_final_kernel(const __grid_constant__ CflBoxTable tab, double cfl,
+                                                              const double* __restrict__ part, double* sdt) {
+  __shared__ double sh[32];
+  __shared__ int anybad;
+  __shared__ double md[3];
+  const CflBoxDev& bx = tab.box[blockIdx.x];
+  if (threadIdx.x == 0) anybad = 0;
+  __syncthreads();
+  for (int d = 0; d < 3; ++d) {
+    double m = 0.0;
+    bool bad = false;
+    for (int i = threadIdx.x; i < bx.nblk; i += blockDim.x) {
+      const double v = part[(long long)d * tab.total + bx.first + i];
+      if (isnan(v)) bad = true;
+      m = fmax(m, v);
+    }
+    if (bad) anybad = 1;
+    m = block_max(m, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) md[d] = m;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double s = md[0] / bx.dx[0];
+    double s1 = md[1] / bx.dx[1];
+    double s2 = md[2] / bx.dx[2];
+    s = s1 > s ? s1 : s;
+    s = s2 > s ? s2 : s;
+    const double mm = anybad ? __longlong_as_double(0x7ff8000000000000LL) : s;
+    const double dt = cfl / mm;
+    *bx.dt = dt;
+    if (bx.smax) *bx.smax = mm;
+    sdt[blockIdx.x] = bx.scale * dt;
+  }
+}
+
+// min over boxes of scale_b dt_b; NaN if any is NaN.
+__global__ void __launch_bounds__(256) cfl_boxes_min_kernel(const double* __restrict__ sdt, int n, double* out) {
+  __shared__ double sh[32];
+  __shared__ int anybad;
+  if (threadIdx.x == 0) anybad = 0;
+  __syncthreads();
+  double m = -__longlong_as_double(0x7ff0000000000000LL);  // max of -dt
+  bool bad = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = sdt[i];
+    if (isnan(v)) bad = true;
+    m = fmax(m, -v);
+  }
+  if (bad) anybad = 1;
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+    *out = anybad ? __longlong_as_double(0x7ff8000000000000LL) : -r;
+  }
+}
+
 // Totals: per-CTA FP64 partial sums of the five variables, then one CTA.
 template <class S>
 __global__ void totals_partial_kernel(const S* __restrict__ U, int G, long long gstride, long long vstride,
@@ -303,6 +428,54 @@ cudaError_t launch_cfl(const void* U, int G, long long gs, long long vs, long lo
   cudaError_t e = launch_cfl_partial(U, G, gs, vs, cells, dbl, gamma, dfl, pfl, ws, grid, st);
   if (e != cudaSuccess) return e;
   return launch_cfl_final(ws, 1, grid, dx, cfl, dt, smax, st);
+}
+
+// Workspace of the many-box reduction: 3 partials per pass-1 CTA (at most
+// RED_MAX_CTAS + CFL_MAX_BOXES CTAs) and one scaled dt per box.
+size_t cfl_boxes_workspace_bytes() { return sizeof(double) * (3 * (RED_MAX_CTAS + CFL_MAX_BOXES) + CFL_MAX_BOXES); }
+
+// Pass-1 CTAs shared out in proportion to the boxes' cells, at least one per
+// box, at most RED_MAX_CTAS + n in all.
+cudaError_t launch_cfl_boxes(const hydro_cfl_box* boxes, int n, int dbl, double gamma, double dfl, double pfl,
+                             double cfl, double* dt_min, double* ws, cudaStream_t st) {
+  CflBoxTable tab;
+  tab.n = n;
+  long long all = 0;
+  for (int b = 0; b < n; ++b) all += (long long)boxes[b].G * boxes[b].cells;
+  // cells per pass-1 CTA: 64 per thread of a 256-thread CTA, more when the
+  // boxes together would need more than RED_MAX_CTAS CTAs
+  long long per = 256LL * 64;
+  if ((all + per - 1) / per > RED_MAX_CTAS) per = (all + RED_MAX_CTAS - 1) / RED_MAX_CTAS;
+  int first = 0;
+  for (int b = 0; b < n; ++b) {
+    CflBoxDev& t = tab.box[b];
+    t.U = boxes[b].U;
+    t.gstride = boxes[b].group_stride;
+    t.vstride = boxes[b].var_stride;
+    t.cells = boxes[b].cells;
+    t.G = boxes[b].G;
+    t.pad = 0;
+    for (int d = 0; d < 3; ++d) t.dx[d] = boxes[b].dx[d];
+    t.dt = boxes[b].dt_dev;
+    t.smax = boxes[b].smax_dev;
+    t.scale = boxes[b].dt_scale;
+    const long long cb = (long long)boxes[b].G * boxes[b].cells;
+    long long nb = (cb + per - 1) / per;
+    if (nb < 1) nb = 1;
+    tab.box[b].first = first;
+    tab.box[b].nblk = (int)nb;
+    first += (int)nb;
+  }
+  tab.total = first;
+  double* part = ws;
+  double* sdt = ws + 3 * (RED_MAX_CTAS + CFL_MAX_BOXES);
+  if (dbl)
+    cfl_boxes_partial_kernel<double><<<first, 256, 0, st>>>(tab, gamma, dfl, pfl, part);
+  else
+    cfl_boxes_partial_kernel<float><<<first, 256, 0, st>>>(tab, gamma, dfl, pfl, part);
+  cfl_boxes_final_kernel<<<n, 256, 0, st>>>(tab, cfl, part, sdt);
+  if (dt_min) cfl_boxes_min_kernel<<<1, 256, 0, st>>>(sdt, n, dt_min);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_totals(const void* U, int G, long long gs, long long vs, long long cells, int dbl, double* out,

@@ -16,6 +16,9 @@ cudaError_t launch_gather(const void* field, int X, int Y, int Z, int bc, const 
 cudaError_t launch_cfl(const void* U, int G, long long gs, long long vs, long long cells, int dbl, double gamma,
                        double dfl, double pfl, const double* dx, double cfl, double* dt, double* smax, double* ws,
                        cudaStream_t st, int nsm);
+size_t cfl_boxes_workspace_bytes();
+cudaError_t launch_cfl_boxes(const hydro_cfl_box* boxes, int n, int dbl, double gamma, double dfl, double pfl,
+                             double cfl, double* dt_min, double* ws, cudaStream_t st);
 cudaError_t launch_totals(const void* U, int G, long long gs, long long vs, long long cells, int dbl, double* out,
                           double* ws, cudaStream_t st, int nsm);
 constexpr int RED_MAX_CTAS = 2048;
@@ -422,6 +425,28 @@ int hydro_cfl_dt(const void* U, int G, long long group_stride, long long var_str
   }
   cudaError_t e = launch_cfl(U, G, group_stride, var_stride, cells, precision == HYDRO_FP64, gamma, dens_floor,
                              pres_floor, dx, cfl, dt_dev, smax_dev, (double*)workspace, (cudaStream_t)stream, nsm);
+  return e == cudaSuccess ? HYDRO_OK : cuda_fail(e);
+}
+
+size_t hydro_cfl_boxes_workspace_bytes(void) { return cfl_boxes_workspace_bytes(); }
+
+int hydro_cfl_dt_boxes(const hydro_cfl_box* boxes, int nbox, int precision, double gamma, double dens_floor,
+                       double pres_floor, double cfl, double* dt_min_dev, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+  if (!boxes || nbox < 1 || nbox > HYDRO_CFL_MAX_BOXES || !(gamma > 1.0) || !(cfl > 0.0)) return HYDRO_EINVAL;
+  if (precision < 0 || precision > 2) return HYDRO_EINVAL;
+  for (int b = 0; b < nbox; ++b) {
+    const hydro_cfl_box& x = boxes[b];
+    if (!x.U || !x.dt_dev || x.G < 0 || x.cells < 0 || !finite_pos(x.dt_scale)) return HYDRO_EINVAL;
+    for (int d = 0; d < 3; ++d)
+      if (!finite_pos(x.dx[d])) return HYDRO_EINVAL;
+  }
+  if (!workspace || workspace_bytes < cfl_boxes_workspace_bytes()) return HYDRO_EWORKSPACE;
+  int dev;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  cudaError_t e = launch_cfl_boxes(boxes, nbox, precision == HYDRO_FP64, gamma, dens_floor, pres_floor, cfl,
+                                   dt_min_dev, (double*)workspace, (cudaStream_t)stream);
   return e == cudaSuccess ? HYDRO_OK : cuda_fail(e);
 }
 

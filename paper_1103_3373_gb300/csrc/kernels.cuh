@@ -6,6 +6,7 @@
 // z-neighbours, and a CTA streams through each run of them as one chain.
 #pragma once
 #include "ctu.cuh"
+#include "ctu_pair.cuh"
 #include "mhm.cuh"
 #include "split.cuh"
 #include "vl.cuh"
@@ -78,7 +79,9 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
     __syncthreads();
     GroupCtx<T, S, N> C;
     C.init(sg, gi, kc, sc);
-    if constexpr (SCH == CTU)
+    if constexpr (SCH == CTU && PR == P_FP32 && !CH)
+      ctu_pair_group<RS, REC, N>(C, o, ring, K, sts);
+    else if constexpr (SCH == CTU)
       ctu_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
     else if constexpr (SCH == MHM)
       mhm_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);

@@ -103,6 +103,14 @@ class Params:
         return p
 
 
+class _CCflBox(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("G", ctypes.c_int), ("group_stride", ctypes.c_longlong),
+                ("var_stride", ctypes.c_longlong), ("cells", ctypes.c_longlong), ("dx", ctypes.c_double * 3),
+                ("dt_dev", ctypes.c_void_p), ("smax_dev", ctypes.c_void_p), ("dt_scale", ctypes.c_double)]
+
+
+CFL_MAX_BOXES = 256
+
 _LIB = None
 
 
@@ -142,6 +150,9 @@ def _lib():
         L.hydro_amr_prepare.argtypes = [A, A, vp, d, i, i, i, i, vp, vp, vp]
         L.hydro_amr_reflux.argtypes = [A, vp, A, vp, vp, d, ctypes.POINTER(ctypes.c_double), i, i, i, vp, vp]
         L.hydro_amr_restrict.argtypes = [A, A, i, i, vp, vp]
+        L.hydro_cfl_boxes_workspace_bytes.argtypes = []
+        L.hydro_cfl_boxes_workspace_bytes.restype = ctypes.c_size_t
+        L.hydro_cfl_dt_boxes.argtypes = [ctypes.POINTER(_CCflBox), i, i, d, d, d, d, vp, vp, ctypes.c_size_t, vp]
         L.hydro_fma_peak.argtypes = [i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_double)]
         L.hydro_strerror.argtypes = [i]
         L.hydro_strerror.restype = ctypes.c_char_p
@@ -400,6 +411,43 @@ def hydro_cfl_dt_noalloc(U, dx, cfl, dt_out, gamma=1.4, dens_floor=0.0, pres_flo
                                      dxa, float(cfl), _ptr(dt_out, "dt_out", "float64"),
                                      _ptr(smax_out, "smax_out", "float64"), _stream(stream))
     _check(rc, "hydro_cfl_dt_noalloc")
+
+
+def hydro_cfl_boxes_workspace_bytes():
+    return int(_lib().hydro_cfl_boxes_workspace_bytes())
+
+
+def make_cfl_boxes(boxes, precision):
+    """ctypes table for hydro_cfl_dt_boxes from (U, dx, dt_out[, dt_scale[,
+    smax_out]]) tuples: U a contiguous field [5,Z,Y,X] or groups
+    [G,5,...]; dt_out / smax_out 1-element float64 device tensors."""
+    dt = _storage_dtype(precision)
+    arr = (_CCflBox * len(boxes))()
+    for k, b in enumerate(boxes):
+        U, dx, dt_out = b[0], b[1], b[2]
+        scale = float(b[3]) if len(b) > 3 else 1.0
+        smax = b[4] if len(b) > 4 else None
+        G, gs, vs, cells = _red_layout(U)
+        e = arr[k]
+        e.U = _ptr(U, "U", dt)
+        e.G, e.group_stride, e.var_stride, e.cells = G, gs, vs, cells
+        for d_ in range(3):
+            e.dx[d_] = float(dx[d_])
+        e.dt_dev = _ptr(dt_out, "dt_out", "float64")
+        e.smax_dev = _ptr(smax, "smax_out", "float64")
+        e.dt_scale = scale
+    return arr
+
+
+def hydro_cfl_dt_boxes(boxes, cfl, workspace, dt_min_out=None, gamma=1.4, dens_floor=0.0, pres_floor=0.0,
+                       precision=FP32, stream=None, _carray=None):
+    """CFL dt of every box in one pass (at most CFL_MAX_BOXES per call); see
+    make_cfl_boxes for the tuples.  dt_min_out receives min_b dt_scale_b dt_b."""
+    arr = _carray if _carray is not None else make_cfl_boxes(boxes, precision)
+    rc = _lib().hydro_cfl_dt_boxes(arr, len(arr), precision, gamma, dens_floor, pres_floor, float(cfl),
+                                   _ptr(dt_min_out, "dt_min_out", "float64"), _ptr(workspace, "workspace"),
+                                   workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "hydro_cfl_dt_boxes")
 
 
 # ---------------------------------------------------------------- peaks (include/hydro_peaks.h)

@@ -208,7 +208,9 @@ class LevelBatch:
             self.dts.append(torch.zeros(1, dtype=torch.float64, device=self.dev))
             self.dx.append((lv["dx"],) * 3)
         self.cells = sum(u.shape[0] for u in self.U_in) * N ** 3
-        self.red_ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=self.dev)
+        self.red_ws = torch.empty(H.hydro_cfl_boxes_workspace_bytes(), dtype=torch.uint8, device=self.dev)
+        self.cfl_boxes = H.make_cfl_boxes([(self.U_in[l], self.dx[l], self.dts[l]) for l in range(len(self.U_in))],
+                                          params.precision)
         self.stream = stream
         self._alloc_ws()
         self.graph = None
@@ -221,11 +223,10 @@ class LevelBatch:
         self.carray = H.make_levels(self.entries, self.p.precision)
 
     def reduce_dt(self, stream=None):
+        """Every level's dt in one device pass (hydro_cfl_dt_boxes)."""
         s = stream if stream is not None else self.stream
-        for l, U in enumerate(self.U_in):
-            H.hydro_cfl_dt(U, self.dx[l], self.cfl, self.dts[l], self.red_ws, gamma=self.p.gamma,
-                           dens_floor=self.p.dens_floor, pres_floor=self.p.pres_floor, precision=self.p.precision,
-                           stream=s)
+        H.hydro_cfl_dt_boxes(None, self.cfl, self.red_ws, gamma=self.p.gamma, dens_floor=self.p.dens_floor,
+                             pres_floor=self.p.pres_floor, precision=self.p.precision, stream=s, _carray=self.cfl_boxes)
 
     def advance_batched(self, stream=None):
         s = stream if stream is not None else self.stream
@@ -399,18 +400,17 @@ class AmrHierarchy:
         return n
 
     def compute_dt(self, cfl=0.4):
-        """min over levels of 2^l x the CFL dt of level l (host value; one
-        device reduction per level)."""
+        """dt_0 = min over levels of 2^l x the CFL dt of level l, reduced on
+        the device in one pass (hydro_cfl_dt_boxes with dt_scale = 2^l);
+        returns the host value."""
         torch = self.torch
-        ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=self.dev)
-        dts = torch.zeros(self.L, dtype=torch.float64, device=self.dev)
+        ws = torch.empty(H.hydro_cfl_boxes_workspace_bytes(), dtype=torch.uint8, device=self.dev)
+        dts = torch.zeros(self.L + 1, dtype=torch.float64, device=self.dev)
         p = self.params[0]
-        for l in range(self.L):
-            H.hydro_cfl_dt(self.cur[l], self.params[l].dx, cfl, dts[l:l + 1], ws, gamma=p.gamma,
-                           dens_floor=p.dens_floor, pres_floor=p.pres_floor, precision=self.prec,
-                           stream=self.stream)
-        scale = torch.tensor([2.0 ** l for l in range(self.L)], dtype=torch.float64, device=self.dev)
-        return float((dts * scale).min().item())
+        boxes = [(self.cur[l], self.params[l].dx, dts[l:l + 1], 2.0 ** l) for l in range(self.L)]
+        H.hydro_cfl_dt_boxes(boxes, cfl, ws, dt_min_out=dts[self.L:], gamma=p.gamma, dens_floor=p.dens_floor,
+                             pres_floor=p.pres_floor, precision=self.prec, stream=self.stream)
+        return float(dts[self.L].item())
 
     def errors(self):
         return int(self.err.item())

@@ -4,11 +4,15 @@ Requests (independent periodic boxes of different sizes, each with its own
 step count) arrive over time.  The engine keeps every admitted box's state
 resident on the device and, at every tick, advances ALL active boxes by one
 step with one persistent launch (hydro_advance_levels, one entry per box with
-its own dx and device dt; chunks of HYDRO_MAX_LEVELS boxes), then reduces each
-box's next dt on the device.  Requests that arrive while others are running
-are admitted at the next tick as soon as the HBM budget allows (FIFO), so new
-work joins the batch in flight instead of waiting for it to drain; finished
-boxes leave the batch and return their memory.
+its own dx and device dt; chunks of HYDRO_MAX_LEVELS boxes), then reduces
+every box's next dt in one pass (hydro_cfl_dt_boxes, chunks of
+HYDRO_CFL_MAX_BOXES boxes).  Requests that arrive while others are running
+are admitted at the next tick (FIFO) as soon as two budgets allow: device
+memory (HBM) and the cells advanced per tick.  The second bounds the length
+of a tick, so the step latency of every request in the batch stays bounded
+under overload while the GPU still gets tens of millions of cell updates per
+launch; new work joins the batch in flight instead of waiting for it to
+drain, and finished boxes leave the batch and return their memory.
 
 A box's result does not depend on what else is in the batch: every group is
 computed by one CTA from its own box's data only, with its own dt.
@@ -38,6 +42,8 @@ class Request:
     # filled by the engine
     t_admit: float = float("nan")
     t_done: float = float("nan")
+    tick_admit: int = -1
+    tick_done: int = -1
     steps_done: int = 0
     result: object = None
 
@@ -83,7 +89,7 @@ class BaseStates:
 
 class ServingEngine:
     def __init__(self, params: H.Params, sizes=(32, 64, 128, 256), budget_bytes=None, cfl=0.4, device="cuda:0",
-                 keep_results=False, max_inflight=2):
+                 keep_results=False, max_inflight=2, max_cells_per_tick=1 << 26):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -96,12 +102,16 @@ class ServingEngine:
             budget_bytes = int(0.5 * free)
         self.budget = budget_bytes
         self.used = 0
+        # cells advanced per tick (a box larger than this still runs, alone)
+        self.max_cells = int(max_cells_per_tick)
+        self.active_cells = 0
         self.queue = collections.deque()
         self.active = []
         self.done = []
         self.keep_results = keep_results
         self.states = BaseStates(sizes, self.dev, self.dtype, gamma=params.gamma)
-        self.red_ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=self.dev)
+        self.red_ws = torch.empty(max(H.hydro_cfl_workspace_bytes(), H.hydro_cfl_boxes_workspace_bytes()),
+                                  dtype=torch.uint8, device=self.dev)
         nws = H.hydro_workspace_bytes(params)
         self.p.workspace = torch.empty(nws, dtype=torch.uint8, device=self.dev) if nws else None
         self.stream = torch.cuda.Stream(device=self.dev)
@@ -121,8 +131,8 @@ class ServingEngine:
         while self.queue and self.queue[0].t_arrive <= now:
             req = self.queue[0]
             need = self.footprint(req.n)
-            if self.used + need > self.budget and self.active:
-                break  # FIFO: wait until memory frees up
+            if self.active and (self.used + need > self.budget or self.active_cells + req.n ** 3 > self.max_cells):
+                break  # FIFO: wait until memory and tick capacity free up
             self.queue.popleft()
             with torch.cuda.stream(self.stream):
                 a = self.states.make(req.n, req.mach, req.seed)
@@ -133,7 +143,9 @@ class ServingEngine:
             H.hydro_cfl_dt(a, box.dx, self.cfl, dt, self.red_ws, gamma=self.p.gamma, dens_floor=self.p.dens_floor,
                            pres_floor=self.p.pres_floor, precision=self.p.precision, stream=self.stream)
             req.t_admit = now
+            req.tick_admit = self.ticks
             self.used += need
+            self.active_cells += req.n ** 3
             self.active.append(box)
 
     def _tick(self):
@@ -150,10 +162,12 @@ class ServingEngine:
             cells += sum(bx.req.n ** 3 for bx in chunk)
         for bx in self.active:
             bx.a, bx.b = bx.b, bx.a
-            H.hydro_cfl_dt(bx.a, bx.dx, self.cfl, bx.dt, self.red_ws, gamma=self.p.gamma,
-                           dens_floor=self.p.dens_floor, pres_floor=self.p.pres_floor, precision=self.p.precision,
-                           stream=self.stream)
             bx.req.steps_done += 1
+        for k in range(0, len(self.active), H.CFL_MAX_BOXES):
+            chunk = self.active[k:k + H.CFL_MAX_BOXES]
+            H.hydro_cfl_dt_boxes([(bx.a, bx.dx, bx.dt) for bx in chunk], self.cfl, self.red_ws, gamma=self.p.gamma,
+                                 dens_floor=self.p.dens_floor, pres_floor=self.p.pres_floor,
+                                 precision=self.p.precision, stream=self.stream)
         e1.record(self.stream)
         self.tick_events.append((e0, e1, cells, len(self.active)))
         self.cell_updates += cells
@@ -169,35 +183,44 @@ class ServingEngine:
                 if self.keep_results:
                     bx.req.result = bx.a.detach().to("cpu")
                 self.used -= bx.bytes
+                self.active_cells -= bx.req.n ** 3
+                bx.req.tick_done = self.ticks
                 self.done.append(bx.req)
             else:
                 still.append(bx)
         self.active = still
 
-    def run(self, requests, realtime=True, t0=None):
-        """Serve `requests` (sorted by arrival).  With realtime the arrival
-        times are wall-clock offsets from the start; otherwise all requests are
-        present at t = 0.  Returns the summary dict."""
+    def run(self, requests, realtime=True, t0=None, clock="wall"):
+        """Serve `requests` (sorted by arrival).  clock="wall": with realtime
+        the arrival times are wall-clock offsets from the start, otherwise
+        all requests are present at t = 0.  clock="ticks": t_arrive is the
+        tick at whose start the request becomes admissible (deterministic:
+        the batch a request joins does not depend on timing).  Returns the
+        summary dict."""
+        ticks = clock == "ticks"
         for r in sorted(requests, key=lambda r: r.t_arrive):
-            if not realtime:
+            if not realtime and not ticks:
                 r.t_arrive = 0.0
             self.submit(r)
         start = time.perf_counter() if t0 is None else t0
-        for r in self.queue:
-            r.t_arrive += start
+        if not ticks:
+            for r in self.queue:
+                r.t_arrive += start
         while self.queue or self.active:
-            now = time.perf_counter()
+            now = float(self.ticks) if ticks else time.perf_counter()
             self._admit(now)
             if self.active:
                 self._tick()
+            elif ticks:
+                self.ticks += 1  # idle tick: nothing admissible yet
             else:
                 nxt = self.queue[0].t_arrive
                 time.sleep(max(0.0, min(0.01, nxt - time.perf_counter())))
         self.torch.cuda.synchronize()
         wall = time.perf_counter() - start
         tick_ms = [a.elapsed_time(b) for a, b, _, _ in self.tick_events]
-        turn = [r.t_done - r.t_arrive for r in self.done]
-        wait = [r.t_admit - r.t_arrive for r in self.done]
+        turn = [r.t_done - r.t_arrive for r in self.done] if not ticks else []
+        wait = [r.t_admit - r.t_arrive for r in self.done] if not ticks else []
         gpu_s = sum(tick_ms) / 1e3
         return {"requests": len(self.done), "ticks": self.ticks, "cell_updates": self.cell_updates,
                 "wall_s": wall, "cell_updates_per_s_wall": self.cell_updates / wall,
@@ -208,7 +231,8 @@ class ServingEngine:
                 "p99_turnaround_s": float(np.percentile(turn, 99)) if turn else None,
                 "p99_queue_wait_s": float(np.percentile(wait, 99)) if wait else None,
                 "max_active": max((n for _, _, _, n in self.tick_events), default=0),
-                "budget_bytes": self.budget}
+                "max_cells_in_a_tick": max((c for _, _, c, _ in self.tick_events), default=0),
+                "budget_bytes": self.budget, "max_cells_per_tick": self.max_cells}
 
 
 def requests_from_arrivals(arrivals):

@@ -114,3 +114,57 @@ def test_serving_admission_respects_budget():
     summ = eng.run(reqs, realtime=False)
     assert summ["requests"] == 6
     assert summ["max_active"] == 3
+
+
+def _req(rid, t, n, mach, steps, seed):
+    return SV.Request(rid=rid, t_arrive=t, n=n, mach=mach, steps=steps, seed=seed)
+
+
+def test_serving_join_in_flight_same_as_alone():
+    """Deterministic tick clock: request 1 becomes admissible at tick 2 while
+    request 0 (admitted at tick 0) is still being stepped, and request 2 at
+    tick 3; each joins the batch in flight, and each result is the same, bit
+    for bit, as the same request run alone."""
+    import torch
+    spec = [(0, 0, 64, 1.2, 6, 21), (1, 2, 32, 2.5, 5, 22), (2, 3, 32, 0.8, 3, 23)]
+    mixed = SV.ServingEngine(_params(), sizes=(32, 64), keep_results=True)
+    mixed.run([_req(*x) for x in spec], clock="ticks")
+    by = {r.rid: r for r in mixed.done}
+    assert by[0].tick_admit == 0 and by[1].tick_admit == 2 and by[2].tick_admit == 3
+    # 1 and 2 joined while 0 was in flight (0 finishes after 6 ticks)
+    assert by[1].tick_admit < by[0].tick_done and by[2].tick_admit < by[0].tick_done
+    for x in spec:
+        alone = SV.ServingEngine(_params(), sizes=(32, 64), keep_results=True)
+        alone.run([_req(*x)], clock="ticks")
+        assert alone.done[0].steps_done == x[4]
+        assert torch.equal(alone.done[0].result, by[x[0]].result)
+
+
+def test_serving_admission_bounds_cells_per_tick():
+    """The work bound: with room for two 64^3 boxes per tick, four requests
+    never run more than two at a time, every tick advances at most 2 x 64^3
+    cells, and every request still completes its steps."""
+    reqs = [_req(i, 0, 64, 1.0, 3, 40 + i) for i in range(4)]
+    eng = SV.ServingEngine(_params(), sizes=(64,), max_cells_per_tick=2 * 64 ** 3)
+    summ = eng.run(reqs, clock="ticks")
+    assert summ["requests"] == 4
+    assert summ["max_active"] == 2
+    assert summ["max_cells_in_a_tick"] <= 2 * 64 ** 3
+    assert all(r.steps_done == 3 for r in eng.done)
+
+
+def test_amr_hierarchy_dt_is_min_over_levels():
+    """dt_0 of an AMR hierarchy (one device pass over the levels) equals the
+    minimum over levels of 2^l times each level's own CFL dt."""
+    import torch
+    levels = W.amr_hierarchy(48, (0.2,))
+    hier = RT.AmrHierarchy(levels, _params())
+    ws = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device="cuda:0")
+    per = []
+    for l in range(hier.L):
+        d = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        p = hier.params[l]
+        H.hydro_cfl_dt(hier.cur[l], p.dx, 0.4, d, ws, gamma=p.gamma, dens_floor=p.dens_floor,
+                       pres_floor=p.pres_floor, precision=hier.prec)
+        per.append((2.0 ** l) * d.item())
+    assert hier.compute_dt(0.4) == min(per)

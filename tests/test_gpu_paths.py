@@ -303,3 +303,47 @@ def test_fma_peak_kernels(torch_dev):
     with pytest.raises(H.HydroError) as e:
         H.hydro_fma_peak(7, 1, 32, 1, torch.empty(32, device=dev))
     assert e.value.code == H.EINVAL
+
+
+@pytest.mark.parametrize("prec", [H.FP64, H.FP32])
+def test_cfl_dt_boxes_equals_per_box(torch_dev, prec):
+    """The many-box CFL reduction (one pass for a list of boxes, Sec. 4.3 per
+    box) gives every box exactly hydro_cfl_dt's dt and max speed, and the
+    scaled minimum over boxes; a NaN box makes its dt and the minimum NaN."""
+    torch, dev = torch_dev
+    dtp = tdtype(prec)
+    fields = [torch.tensor(quantise(W.lognormal(n, seed=30 + n, mach=0.5 + n / 64), prec), dtype=dtp, device=dev)
+              for n in (32, 64, 16, 48)]
+    grouped = torch.tensor(lognormal_groups(n=32, g=3, seed=7, prec=prec)[1], dtype=dtp, device=dev)
+    Us = fields + [grouped]
+    dxs = [(1 / 32, 1 / 30, 1 / 34), (1 / 64,) * 3, (0.1, 0.2, 0.3), (1 / 48,) * 3, (1 / 40,) * 3]
+    scales = [1.0, 2.0, 4.0, 0.5, 8.0]
+    ws1 = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    ref_dt = torch.zeros(len(Us), dtype=torch.float64, device=dev)
+    ref_sm = torch.zeros(len(Us), dtype=torch.float64, device=dev)
+    for k, U in enumerate(Us):
+        H.hydro_cfl_dt(U, dxs[k], 0.45, ref_dt[k:k + 1], ws1, precision=prec, smax_out=ref_sm[k:k + 1])
+    ws = torch.empty(H.hydro_cfl_boxes_workspace_bytes(), dtype=torch.uint8, device=dev)
+    dt = torch.full((len(Us) + 1,), float("nan"), dtype=torch.float64, device=dev)
+    sm = torch.full((len(Us),), float("nan"), dtype=torch.float64, device=dev)
+    boxes = [(U, dxs[k], dt[k:k + 1], scales[k], sm[k:k + 1]) for k, U in enumerate(Us)]
+    H.hydro_cfl_dt_boxes(boxes, 0.45, ws, dt_min_out=dt[len(Us):], precision=prec)
+    torch.cuda.synchronize()
+    a, b = dt.cpu().numpy(), ref_dt.cpu().numpy()
+    np.testing.assert_array_equal(a[:-1], b)
+    np.testing.assert_array_equal(sm.cpu().numpy(), ref_sm.cpu().numpy())
+    assert a[-1] == min(s * x for s, x in zip(scales, b))
+    # a NaN cell in one box: that box's dt and the minimum are NaN, the others unchanged
+    Us[1].view(-1)[12345] = float("nan")
+    H.hydro_cfl_dt_boxes(boxes, 0.45, ws, dt_min_out=dt[len(Us):], precision=prec)
+    torch.cuda.synchronize()
+    a = dt.cpu().numpy()
+    assert np.isnan(a[1]) and np.isnan(a[-1])
+    np.testing.assert_array_equal(np.delete(a[:-1], 1), np.delete(b, 1))
+    # argument errors
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_cfl_dt_boxes([], 0.45, ws)
+    assert e.value.code == H.EINVAL
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_cfl_dt_boxes(boxes[:1], 0.45, ws1[:64])
+    assert e.value.code == H.EWORKSPACE
