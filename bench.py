@@ -530,6 +530,8 @@ def main():
                          "R = 0.25, mixed vs FP64, about half an hour)")
     ap.add_argument("--block-threads", type=int, default=0,
                     help="use this many threads per CTA (capped per kernel) instead of autotuning")
+    ap.add_argument("--chain", type=int, default=-1,
+                    help="with --block-threads: chain length / z-segment of the work order (0 = whole columns)")
     args = ap.parse_args()
     if args.quick:
         args.no_extra = args.no_cpu = True
@@ -567,7 +569,8 @@ def main():
     box = RT.UniformBox(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev, stream=stream)
     if args.block_threads:
         box.p.block_threads = args.block_threads
-        tuned = {"block_threads": args.block_threads, "grid_ctas": 0, "fixed": True}
+        box.p.chain = max(0, args.chain)
+        tuned = {"block_threads": args.block_threads, "grid_ctas": 0, "chain": box.p.chain, "fixed": True}
     else:
         tuned = box.tune()
     box.compute_dt()
@@ -689,13 +692,14 @@ def main():
             if args.block_threads:
                 # a fixed launch shape (profiling): no tuning launches
                 bx.p.block_threads = min(args.block_threads, H.hydro_max_block_threads(bx.p))
-                tb = {"block_threads": bx.p.block_threads}
+                bx.p.chain = max(0, args.chain)
+                tb = {"block_threads": bx.p.block_threads, "chain": bx.p.chain}
             else:
                 tb = bx.tune()
             bx.compute_dt()
             sm, am, tm, _ = time_box(bx, 50, 3, torch)
             extra[tag] = {"value": cells * 50 / (tm / 1e3), "unit": UNIT, "ms_per_step": tm / 50,
-                          "kernel_ms": am, "block_threads": tb["block_threads"],
+                          "kernel_ms": am, "block_threads": tb["block_threads"], "chain": tb.get("chain", 0),
                           "roofline": leg_roofline(fkey, am, peak, fp32_note)}
             del bx
         torch.cuda.empty_cache()
@@ -720,7 +724,8 @@ def main():
                 "step_latency_samples": len(step_ms),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 3 * args.steps,
-                "autotuned": {"block_threads": tuned["block_threads"], "grid_ctas": tuned["grid_ctas"]},
+                "autotuned": {"block_threads": tuned["block_threads"], "grid_ctas": tuned["grid_ctas"],
+                              "chain": tuned.get("chain", 0)},
                 "status_error_groups": int(np.count_nonzero(st & H.ST_ERROR_MASK)),
                 "state_finite": finite, "extra": extra,
                 "paper_context": "3.0e7 cell-updates/s, CTU+PPM+Roe FP32 on one Tesla C2050 incl. transfers "

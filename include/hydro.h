@@ -106,6 +106,16 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge
  *   split_order  HYDRO_RTVD / HYDRO_WAF only: the sweeps of a step run
  *                x, y, z (0) or z, y, x (1); alternate them between steps
  *                (Strang).  The other schemes ignore it.
+ *   chain        uniform fields (hydro_advance_uniform*, mode-1 levels) of
+ *                the unsplit schemes: a CTA streams through runs of up to
+ *                `chain` z-consecutive groups without restarting (the ghost
+ *                planes between them are traced and solved once), 1 <= chain
+ *                <= HYDRO_CHAIN_MAX; 0 = min(group layers, HYDRO_CHAIN_MAX).
+ *                The work list takes the box in z-segments of `chain`
+ *                layers, every column's first segment before any second
+ *                one, so CTAs on neighbouring columns pass the same layers
+ *                at about the same time and share their halo planes in L2.
+ *                Results do not depend on it (the autotuner picks it).
  *
  * The split schemes (the directionally split comparison schemes of Sec.
  * 3.2): RTVD = relaxing TVD in the flux-split form of Trac & Pen (2003),
@@ -125,6 +135,7 @@ typedef struct hydro_params {
   size_t workspace_bytes;
   int characteristic;
   int split_order;
+  int chain;
 } hydro_params;
 
 /* Ghost layers the scheme needs (Sec. 2): MHM and CTU 2 (PLM) / 3 (PPM);
@@ -213,6 +224,7 @@ typedef struct hydro_level {
 
 /* Most entries one hydro_advance_levels call accepts. */
 #define HYDRO_MAX_LEVELS 32
+#define HYDRO_CHAIN_MAX 32
 
 /*
  * hydro_advance_levels — one persistent launch that advances uneven per-AMR-

@@ -19,8 +19,41 @@ struct SegDesc {
   double dx[3];
   int G, mode, bc, X, Y, Z, GX, GY, GZ;
   int gz0;              // mode 1: first group layer of the entry (its GZ layers follow)
+  int lc;               // mode 1: z-segment length of the work order (1..CHAIN_MAX)
   int first;            // flat index of this entry's first group
 };
+
+// Position of work item gi of a mode-1 entry.  Order: z-segments of lc
+// group layers (the last one GZ % lc layers if that is not 0), all columns'
+// segment s before any segment s+1; within a segment column by column, z
+// fastest.  col = gx + GX gy; gz relative to the entry; left = items to the
+// end of the segment (the longest chain that may start at gi).
+struct SegPos {
+  int col, gz, left;
+};
+__device__ __forceinline__ SegPos seg_pos(const SegDesc& sg, int gi) {
+  const int ncol = sg.GX * sg.GY;
+  const int lc = sg.lc;
+  const int full = sg.GZ / lc;
+  const int nfull = full * ncol * lc;
+  SegPos p;
+  if (gi < nfull) {
+    const int zs = gi / (ncol * lc);
+    const int r = gi - zs * ncol * lc;
+    p.col = r / lc;
+    const int zi = r - p.col * lc;
+    p.gz = zs * lc + zi;
+    p.left = lc - zi;
+  } else {
+    const int rem = sg.GZ - full * lc;
+    const int r = gi - nfull;
+    p.col = r / rem;
+    const int zi = r - p.col * rem;
+    p.gz = full * lc + zi;
+    p.left = rem - zi;
+  }
+  return p;
+}
 
 // Longest run of z-consecutive groups of a uniform field that one CTA streams
 // through without restarting (the ring buffers carry over from one group to
@@ -44,9 +77,10 @@ struct KConst {
 // uniform field (mode 1) the context may cover a chain of groups stacked
 // along z; plane z of the chain then belongs to group z / N of the chain.
 //
-// Work order: mode 0 entries in list order; mode 1 entries column by column
-// (z fastest), so that consecutive work items are z-neighbours.  The user's
-// group index (flux and status arrays) is x-fastest:
+// Work order: mode 0 entries in list order; mode 1 entries in z-segments
+// (seg_pos), z fastest within a segment, so that consecutive work items are
+// z-neighbours.  The user's group index (flux and status arrays) is
+// x-fastest:
 //   gu = gx + GX (gy + GY gz).
 template <class T, class S, int N> struct GroupCtx {
   const S* in;
@@ -85,8 +119,9 @@ template <class T, class S, int N> struct GroupCtx {
       Y = sg.Y;
       Z = sg.Z;
       XYZ = (long long)X * Y * Z;
-      int gz = sg.gz0 + gi % sg.GZ;
-      int col = gi / sg.GZ;
+      const SegPos sp = seg_pos(sg, gi);
+      int gz = sg.gz0 + sp.gz;
+      int col = sp.col;
       int gx = col % sg.GX;
       int gy = col / sg.GX;
       ox = gx * N;

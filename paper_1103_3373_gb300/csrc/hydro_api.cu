@@ -109,7 +109,7 @@ int device_sms(State& s, int dev) {
 }
 
 bool valid_enums(const hydro_params* p) {
-  return p->scheme >= 0 && p->scheme <= 4 && p->recon >= 0 && p->recon <= 1 && p->limiter >= 0 && p->limiter <= 3 &&
+  return p->chain >= 0 && p->chain <= HYDRO_CHAIN_MAX && p->scheme >= 0 && p->scheme <= 4 && p->recon >= 0 && p->recon <= 1 && p->limiter >= 0 && p->limiter <= 3 &&
          (p->characteristic == 0 || p->characteristic == 1) && (p->split_order == 0 || p->split_order == 1) &&
          p->riemann >= 0 && p->riemann <= 3 && p->precision >= 0 && p->precision <= 2 &&
          (p->riemann != HYDRO_RS_ROE ||
@@ -195,6 +195,21 @@ int launch_table(const hydro_params* p, const WorkTable& wt, int N, int ghost, v
 
 bool finite_pos(double a) { return a > 0.0 && a < 1e300; }
 
+// z-segment length of a mode-1 entry of GZ group layers
+int segment_layers(const hydro_params* p, int GZ) {
+  int lc = p->chain > 0 ? p->chain : CHAIN_MAX;
+  if (lc > GZ) lc = GZ;
+  return lc < 1 ? 1 : lc;
+}
+
+// [a, a + na) and [b, b + nb) share a byte
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return na > 0 && nb > 0 && x < y + nb && y < x + na;
+}
+
+size_t elem_size(const hydro_params* p) { return p->precision == HYDRO_FP64 ? 8 : 4; }
+
 }  // namespace
 
 extern "C" {
@@ -229,7 +244,12 @@ int hydro_advance(const hydro_params* p, const void* U_in, void* U_out, void* fl
   if (!valid_enums(p) || !valid_physics(p)) return HYDRO_EINVAL;
   int req = hydro_required_ghost(p->scheme, p->recon);
   if (ghost < req) return HYDRO_EGHOST;
-  if (G > 0 && (!U_in || !U_out || U_in == U_out)) return HYDRO_EINVAL;
+  if (G > 0 && (!U_in || !U_out)) return HYDRO_EINVAL;
+  {
+    const size_t M = (size_t)N + 2 * (size_t)ghost;
+    if (overlap(U_in, (size_t)G * 5 * M * M * M * elem_size(p), U_out, (size_t)G * 5 * N * N * N * elem_size(p)))
+      return HYDRO_EINVAL;
+  }
   if (!p->dt_dev && !(p->dt >= 0.0)) return HYDRO_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (!finite_pos(p->dx[d])) return HYDRO_EINVAL;
@@ -257,7 +277,9 @@ int hydro_advance_uniform(const hydro_params* p, const void* field_in, void* fie
   if (N != 16) return HYDRO_EUNSUPPORTED;
   if (X <= 0 || Y <= 0 || Z <= 0 || X % N || Y % N || Z % N) return HYDRO_EINVAL;
   if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
-  if (!field_in || !field_out || field_in == field_out) return HYDRO_EINVAL;
+  if (!field_in || !field_out) return HYDRO_EINVAL;
+  if (overlap(field_in, (size_t)5 * X * Y * Z * elem_size(p), field_out, (size_t)5 * X * Y * Z * elem_size(p)))
+    return HYDRO_EINVAL;
   if (!p->dt_dev && !(p->dt >= 0.0)) return HYDRO_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (!finite_pos(p->dx[d])) return HYDRO_EINVAL;
@@ -284,6 +306,7 @@ int hydro_advance_uniform(const hydro_params* p, const void* field_in, void* fie
   s.GX = X / N;
   s.GY = Y / N;
   s.GZ = Z / N;
+  s.lc = segment_layers(p, s.GZ);
   s.first = 0;
   return launch_table(p, wt, N, hydro_required_ghost(p->scheme, p->recon), stream);
 }
@@ -296,7 +319,9 @@ int hydro_advance_uniform_zrange(const hydro_params* p, const void* field_in, vo
   if (X <= 0 || Y <= 0 || Z <= 0 || X % N || Y % N || Z % N) return HYDRO_EINVAL;
   if (z_begin < 0 || z_end > Z || z_begin > z_end || z_begin % N || z_end % N) return HYDRO_EINVAL;
   if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
-  if (!field_in || !field_out || field_in == field_out) return HYDRO_EINVAL;
+  if (!field_in || !field_out) return HYDRO_EINVAL;
+  if (overlap(field_in, (size_t)5 * X * Y * Z * elem_size(p), field_out, (size_t)5 * X * Y * Z * elem_size(p)))
+    return HYDRO_EINVAL;
   if (!p->dt_dev && !(p->dt >= 0.0)) return HYDRO_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (!finite_pos(p->dx[d])) return HYDRO_EINVAL;
@@ -323,6 +348,7 @@ int hydro_advance_uniform_zrange(const hydro_params* p, const void* field_in, vo
   s.GX = X / N;
   s.GY = Y / N;
   s.GZ = (z_end - z_begin) / N;
+  s.lc = segment_layers(p, s.GZ);
   s.gz0 = z_begin / N;
   s.first = 0;
   return launch_table(p, wt, N, hydro_required_ghost(p->scheme, p->recon), stream);
@@ -363,8 +389,15 @@ int hydro_advance_levels(const hydro_params* p, const hydro_level* levels, int n
       s.GX = lv.X / N;
       s.GY = lv.Y / N;
       s.GZ = lv.Z / N;
+      s.lc = segment_layers(p, s.GZ);
     }
-    if (G > 0 && (!lv.U_in || !lv.U_out || lv.U_in == lv.U_out)) return HYDRO_EINVAL;
+    if (G > 0 && (!lv.U_in || !lv.U_out)) return HYDRO_EINVAL;
+    {
+      const size_t M = (size_t)N + 2 * (size_t)ghost;
+      const size_t nin = lv.mode == 0 ? (size_t)G * 5 * M * M * M : (size_t)5 * lv.X * lv.Y * lv.Z;
+      const size_t nout = lv.mode == 0 ? (size_t)G * 5 * N * N * N : nin;
+      if (overlap(lv.U_in, nin * elem_size(p), lv.U_out, nout * elem_size(p))) return HYDRO_EINVAL;
+    }
     s.in = lv.U_in;
     s.out = lv.U_out;
     s.flux = lv.flux;

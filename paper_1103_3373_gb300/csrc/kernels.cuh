@@ -6,7 +6,6 @@
 // z-neighbours, and a CTA streams through each run of them as one chain.
 #pragma once
 #include "ctu.cuh"
-#include "ctu_pair.cuh"
 #include "mhm.cuh"
 #include "split.cuh"
 #include "vl.cuh"
@@ -71,7 +70,7 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
     const int gi = w - sg.first;
     int K = 1;
     if (sg.mode == 1 && SCH <= CTU) {
-      const int left = sg.GZ - gi % sg.GZ;  // groups left in this column
+      const int left = seg_pos(sg, gi).left;  // groups left in this z-segment
       K = wend - w < left ? wend - w : left;
       K = K < CHAIN_MAX ? K : CHAIN_MAX;
     }
@@ -79,9 +78,7 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
     __syncthreads();
     GroupCtx<T, S, N> C;
     C.init(sg, gi, kc, sc);
-    if constexpr (SCH == CTU && PR == P_FP32 && !CH)
-      ctu_pair_group<RS, REC, N>(C, o, ring, K, sts);
-    else if constexpr (SCH == CTU)
+    if constexpr (SCH == CTU)
       ctu_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
     else if constexpr (SCH == MHM)
       mhm_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);

@@ -50,7 +50,7 @@ class _CParams(ctypes.Structure):
                 ("dx", ctypes.c_double * 3), ("dens_floor", ctypes.c_double), ("pres_floor", ctypes.c_double),
                 ("dt_dev", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("characteristic", ctypes.c_int), ("split_order", ctypes.c_int)]
+                ("characteristic", ctypes.c_int), ("split_order", ctypes.c_int), ("chain", ctypes.c_int)]
 
 
 class _CLevel(ctypes.Structure):
@@ -86,11 +86,12 @@ class Params:
     workspace: object = None
     characteristic: int = 0  # 1: PLM / PPM on characteristic variables (Sec. 2)
     split_order: int = 0     # RTVD / WAF: sweeps x, y, z (0) or z, y, x (1)
+    chain: int = 0           # uniform fields: z-segment / chain length (0 = whole columns, <= CHAIN_MAX)
 
     def c(self):
         p = _CParams()
         for k in ("scheme", "recon", "limiter", "riemann", "roe_fallback", "precision", "block_threads",
-                  "grid_ctas", "characteristic", "split_order"):
+                  "grid_ctas", "characteristic", "split_order", "chain"):
             setattr(p, k, int(getattr(self, k)))
         for k in ("theta", "gamma", "dt", "dens_floor", "pres_floor"):
             setattr(p, k, float(getattr(self, k)))
@@ -110,6 +111,7 @@ class _CCflBox(ctypes.Structure):
 
 
 CFL_MAX_BOXES = 256
+CHAIN_MAX = 32
 
 _LIB = None
 

@@ -85,8 +85,9 @@ def test_chained_columns_equal_single_groups(torch_dev, prec, bc, scheme, recon,
     """In a uniform field a CTA streams through runs of z-consecutive groups
     (chains of at most 32) without restarting.  Field, boundary fluxes and the
     status of every group equal those of the same groups advanced one by one
-    (gather + hydro_advance), whatever the grid (chains cut at other places)
-    and for columns longer than the longest chain.  A double rarefaction
+    (gather + hydro_advance), whatever the grid and the chain length (the
+    z-segments of the work order; chains cut at other places) and for columns
+    longer than the longest chain.  A double rarefaction
     along z centred on a group boundary (and one along x) makes Roe's
     linearisation fail near the boundaries, so the fallback bit is set in
     some groups and must land in the same groups."""
@@ -123,8 +124,10 @@ def test_chained_columns_equal_single_groups(torch_dev, prec, bc, scheme, recon,
     ref_fl, ref_st = fl.cpu().numpy(), st.cpu().numpy()
     fb = (ref_st & H.ST_ROE_FALLBACK) != 0
     assert fb.any() and not fb.all()
-    for grid in (1, 5, 7, 0):
-        ph.grid_ctas = grid
+    # grid sizes and chain lengths (z-segments of the work order) cut the
+    # chains at other places
+    for grid, chain in ((1, 0), (5, 3), (7, 8), (0, 0), (0, 1), (0, 5), (11, 32)):
+        ph.grid_ctas, ph.chain = grid, chain
         with_workspace(ph, dev)
         out = torch.full_like(ft, float("nan"))
         fl2 = torch.full_like(fl, float("nan"))
@@ -225,7 +228,7 @@ def test_edge_cases_and_errors(torch_dev):
     U_in = torch.zeros((1, 5, 22, 22, 22), dtype=torch.float32, device=dev)
     U_out = torch.zeros((1, 5, N, N, N), dtype=torch.float32, device=dev)
     bad = [dict(scheme=7), dict(riemann=9), dict(gamma=1.0), dict(theta=3.0), dict(block_threads=100),
-           dict(block_threads=1024), dict(dx=(0.0, 1.0, 1.0))]
+           dict(block_threads=1024), dict(dx=(0.0, 1.0, 1.0)), dict(chain=-1), dict(chain=H.CHAIN_MAX + 1)]
     for kw in bad:
         _, p = params_pair(O.CTU, O.PPM, O.ROE, H.FP32, 1e-3, (1 / 32,) * 3)
         for k, v in kw.items():
@@ -233,6 +236,15 @@ def test_edge_cases_and_errors(torch_dev):
         with pytest.raises(H.HydroError) as e:
             H.hydro_advance(p, U_in, U_out)
         assert e.value.code == H.EINVAL
+    # output overlapping the input (not only the same base address): refused
+    big = torch.zeros(2 * 5 * 22 ** 3, dtype=torch.float32, device=dev)
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_advance(ph, big[:5 * 22 ** 3].view(1, 5, 22, 22, 22), big[1000:1000 + 5 * N ** 3].view(1, 5, N, N, N))
+    assert e.value.code == H.EINVAL
+    fld = torch.zeros(2 * 5 * 32 ** 3, dtype=torch.float32, device=dev)
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_advance_uniform(ph, fld[:5 * 32 ** 3].view(5, 32, 32, 32), fld[64:64 + 5 * 32 ** 3].view(5, 32, 32, 32))
+    assert e.value.code == H.EINVAL
     _, p = params_pair(O.VL, O.PPM, O.ROE, H.FP32, 1e-3, (1 / 32,) * 3)  # needs 4 ghost layers
     with pytest.raises(H.HydroError) as e:
         H.hydro_advance(p, U_in, U_out, ghost=3)
@@ -345,5 +357,5 @@ def test_cfl_dt_boxes_equals_per_box(torch_dev, prec):
         H.hydro_cfl_dt_boxes([], 0.45, ws)
     assert e.value.code == H.EINVAL
     with pytest.raises(H.HydroError) as e:
-        H.hydro_cfl_dt_boxes(boxes[:1], 0.45, ws1[:64])
+        H.hydro_cfl_dt_boxes(boxes[:1], 0.45, ws1[:64], precision=prec)
     assert e.value.code == H.EWORKSPACE
