@@ -460,6 +460,37 @@ def sedov_long_study(n=512, sub=288, radii=(0.05, 0.10, 0.15, 0.20, 0.25), cfl=0
     return rows
 
 
+def record_traffic(csv_path, command=""):
+    """data/ncu_traffic.json from an ncu --csv launch list of advance_kernel
+    launches of the benchmark box (DRAM read + write bytes per launch)."""
+    import csv
+    import io
+    txt = open(csv_path).read()
+    rows = list(csv.DictReader(io.StringIO(txt[txt.index('"ID"'):])))
+    per = {}
+    for r in rows:
+        if "advance_kernel" not in r.get("Kernel Name", ""):
+            continue
+        if r["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            v = float(r["Metric Value"].replace(",", ""))
+            unit = r.get("Metric Unit", "byte")
+            scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit, 1.0)
+            per[r["ID"]] = per.get(r["ID"], 0.0) + v * scale
+    if not per:
+        raise SystemExit("no advance_kernel DRAM metrics in " + csv_path)
+    launches = [per[k] for k in sorted(per, key=int)]
+    out = {"source_sha": source_hash(),
+           "kernel": "advance_kernel<CTU,PPM,ROE,FP32,16>, 256^3 periodic box, fused gather, chained columns",
+           "bytes_per_launch": launches, "bytes_per_cell": float(np.mean(launches)) / N_BOX ** 3,
+           "source_csv": os.path.basename(csv_path),
+           "note": "dram__bytes_read.sum + dram__bytes_write.sum per launch; valid only while source_sha matches "
+                   "the headline kernel's sources"}
+    with open(os.path.join(ROOT, "paper_1103_3373_gb300", "data", "ncu_traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(out))
+    return 0
+
+
 def reference_arm(args, rank, world):
     """--impl reference: the oracle (FP64 CPU), as it stands, on the host cores."""
     if rank != 0:
@@ -525,6 +556,10 @@ def main():
     ap.add_argument("--legs", default="all",
                     help="comma list of extra legs to run: precisions, schemes, amr_levels, amr_hierarchy, "
                          "serving (default all)")
+    ap.add_argument("--record-traffic", default="",
+                    help="write the headline kernel's DRAM bytes per launch from this ncu CSV (the launch-list "
+                         "capture with dram__bytes_read.sum and dram__bytes_write.sum) to data/ncu_traffic.json, "
+                         "stamped with the hash of the kernel's sources, and exit")
     ap.add_argument("--study", default="", choices=["", "sedov_long"],
                     help="run only this long study instead of the benchmark (sedov_long: the Sedov blast to "
                          "R = 0.25, mixed vs FP64, about half an hour)")
@@ -539,6 +574,8 @@ def main():
     rank, world, local = replicas.rank_info()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.record_traffic:
+        return record_traffic(args.record_traffic)
     if args.study == "sedov_long":
         from paper_1103_3373_gb300 import build as hb
         hb.build()

@@ -9,20 +9,15 @@
 // In a uniform field the CTA streams through a chain of K groups stacked
 // along z (planes 0..KN-1) without restarting.
 //
-// The planes -1-S..-1+S are loaded first.  The stages are pipelined across
-// planes so that one iteration is ONE barrier interval: with pB = t-1,
-//   A  global reads of the input plane pA = pB+S+1 (and of U^n of plane
-//      pB-3) issued into registers first;
-//   B  reconstruct + predict the 6 face states of the cells [-1,N]^2 of
-//      plane pB (one item per cell, the heaviest work);
-//   C  final fluxes of plane pB-1: its x/y faces and the z faces below it
-//      (face states of planes pB-2 and pB-1, made by earlier iterations);
-//   F  update of plane pB-3 (its fluxes are complete);
-//   A  the read plane converted to primitives and stored in its ring slot
-//      (the ring holds 2S+2 planes, so no plane B reads is overwritten).
-// The rings are one plane deeper than a two-interval schedule needs (face
-// states 2 / 3 planes, final fluxes 3).  B items go to the first threads,
-// C items to the others, so every thread gets about the same work.
+// The planes -1-S..-1+S are loaded first; iteration t then runs two barrier
+// intervals for the plane pB = t-1:
+//   1  F  update of plane pB-2 (its fluxes are complete);
+//      B  reconstruct + predict the 6 face states of the cells [-1,N]^2 of
+//         plane pB;
+//   2  A  global reads of the input plane pA = pB+S+1 issued into registers,
+//      C  final fluxes: x/y faces of plane pB, z faces below it,
+//      A  then converted to primitives and stored in the ring (in the slot
+//         of plane pB-S, which B has finished with).
 #pragma once
 #include "stages.cuh"
 
@@ -31,9 +26,8 @@ namespace hyd {
 template <int N, int S> struct MhmLayout {
   static constexpr int L = N + 2;
   static constexpr int LW = N + 2 + 2 * S;
-  static constexpr int RW = 2 * S + 2;  // W ring depth
-  using WR = PlaneRing<float, LW, RW>;
-  using FRf = FaceRings<float, N, 2, 3, 3>;
+  using WR = PlaneRing<float, LW, 2 * S + 1>;
+  using FRf = FaceRings<float, N, 1, 2>;
   static constexpr int OFF_FR = WR::ELEMS;
   static constexpr int TOTAL = OFF_FR + FRf::ELEMS;
 };
@@ -88,111 +82,78 @@ __device__ __forceinline__ void mhm_faces(const WRing& Wr, int p, int jj, int ii
   }
 }
 
-// Prediction item of cell (jj, ii) of plane pB (step (1) of MHM): the six
-// reconstructed face states advanced by dt/2 with the physical-flux
-// differences of all three directions.
-template <int REC, bool CH, class T, class WRing, class FR>
-__device__ __forceinline__ void mhm_predict(const WRing& Wr, const FR& R, int pB, int jj, int ii, const Opts<T>& o,
-                                            T h0, T h1, T h2) {
-  T Uf[3][2][5], Ff[3][2][5];
-  mhm_faces<0, REC, CH>(Wr, pB, jj, ii, o, Uf[0], Ff[0]);
-  mhm_faces<1, REC, CH>(Wr, pB, jj, ii, o, Uf[1], Ff[1]);
-  mhm_faces<2, REC, CH>(Wr, pB, jj, ii, o, Uf[2], Ff[2]);
-  // S = dt/(2dx) (Fx(R) - Fx(L)) + dt/(2dy) (...) + dt/(2dz) (...)
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    T Sv = h0 * (Ff[0][1][v] - Ff[0][0][v]) + h1 * (Ff[1][1][v] - Ff[1][0][v]) + h2 * (Ff[2][1][v] - Ff[2][0][v]);
-    R.XY(pB, 0, 0, v, jj, ii) = Uf[0][0][v] - Sv;
-    R.XY(pB, 0, 1, v, jj, ii) = Uf[0][1][v] - Sv;
-    R.XY(pB, 1, 0, v, jj, ii) = Uf[1][0][v] - Sv;
-    R.XY(pB, 1, 1, v, jj, ii) = Uf[1][1][v] - Sv;
-    R.Zs(pB, 0, v, jj, ii) = Uf[2][0][v] - Sv;
-    R.Zs(pB, 1, v, jj, ii) = Uf[2][1][v] - Sv;
-  }
-}
-
 template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N>
 __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = MhmLayout<N, S_>;
-  constexpr int L = Lay::L, LL = L * L, LW = Lay::LW, RW = Lay::RW;
-  PlaneRing<T, LW, RW> Wr{ring};
-  FaceRings<T, N, 2, 3, 3> R{ring + Lay::OFF_FR};
+  constexpr int L = Lay::L, LL = L * L, LW = Lay::LW;
+  PlaneRing<T, LW, 2 * S_ + 1> Wr{ring};
+  FaceRings<T, N, 1, 2> R{ring + Lay::OFF_FR};
   const T h0 = C.hdtdx[0], h1 = C.hdtdx[1], h2 = C.hdtdx[2];
   const int NP = K * N;
   const int tid = threadIdx.x, nthr = blockDim.x;
 
-  for (int p = -1 - S_; p <= -1 + S_; ++p) stage_load<true, T, S, MIXED, N, LW, RW>(C, o, p, 1 + S_, Wr);
+  for (int p = -1 - S_; p <= -1 + S_; ++p) stage_load<true, T, S, MIXED, N, LW, 2 * S_ + 1>(C, o, p, 1 + S_, Wr);
   __syncthreads();
 
-  const int T_ITERS = NP + 4;
+  const int T_ITERS = NP + 3;
   for (int t = 0; t < T_ITERS; ++t) {
-    const int pB = t - 1;      // predicted
-    const int pE = pB - 1;     // final fluxes
-    const int pF = pB - 3;     // updated
-    const int pA = pB + S_ + 1;  // loaded
-    const int nb = pB <= NP ? LL : 0;
-    const int nx = (pE >= 0 && pE < NP) ? N * (N + 1) : 0;
-    const int ne = (pE >= 0 && pE <= NP) ? 2 * nx + N * N : 0;
-    const int nf = (pF >= 0 && pF < NP) ? N * N : 0;
-    const int na = pA <= NP + S_ ? LW * LW : 0;
-    // A, F: global reads first, consumed at the end
-    T Ua0[5], Un0[5];
-    if (tid < na) {
-      const int jj = tid / LW, ii = tid - jj * LW;
-      C.load5(ii - 1 - S_, jj - 1 - S_, pA, Ua0);
-    }
-    if (tid < nf) {
-      const int j = tid / N, i = tid - j * N;
+    const int pB = t - 1;
+    const int pF = pB - 2;
+    const int pA = pB + S_ + 1;
+    // ---- 1: F (update of plane pF) and B (prediction of plane pB) ---------
+    if (pF >= 0 && pF < NP) stage_update<T, S, MIXED, N>(C, o, R, pF, K, sts);
+    if (pB <= NP) {
+      for (int idx = tid; idx < LL; idx += nthr) {
+        int jj = idx / L, ii = idx - jj * L;
+        T Uf[3][2][5], Ff[3][2][5];
+        mhm_faces<0, REC, CH>(Wr, pB, jj, ii, o, Uf[0], Ff[0]);
+        mhm_faces<1, REC, CH>(Wr, pB, jj, ii, o, Uf[1], Ff[1]);
+        mhm_faces<2, REC, CH>(Wr, pB, jj, ii, o, Uf[2], Ff[2]);
+        // S = dt/(2dx) (Fx(R) - Fx(L)) + dt/(2dy) (...) + dt/(2dz) (...)
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Un0[v] = (T)C.load_raw(v, i, j, pF);
-    }
-    // B on threads [0, nb), C on the rest (a C item is about a quarter of a
-    // B item); with too few threads left for C, one flat loop over both
-    const int nwc = nthr - nb;
-    if (nwc >= 32 && 4 * nwc >= nthr) {
-      if (tid < nb) {
-        const int jj = tid / L, ii = tid - jj * L;
-        mhm_predict<REC, CH>(Wr, R, pB, jj, ii, o, h0, h1, h2);
-      } else {
-        for (int k = tid - nb; k < ne; k += nwc) flux2_item<T, S, MIXED, RS, N>(C, o, R, pE, K, sts, k, nx);
-      }
-    } else {
-      for (int k = tid; k < nb + ne; k += nthr) {
-        if (k < nb) {
-          const int jj = k / L, ii = k - jj * L;
-          mhm_predict<REC, CH>(Wr, R, pB, jj, ii, o, h0, h1, h2);
-        } else {
-          flux2_item<T, S, MIXED, RS, N>(C, o, R, pE, K, sts, k - nb, nx);
+        for (int v = 0; v < 5; ++v) {
+          T Sv = h0 * (Ff[0][1][v] - Ff[0][0][v]) + h1 * (Ff[1][1][v] - Ff[1][0][v]) + h2 * (Ff[2][1][v] - Ff[2][0][v]);
+          R.XY(pB, 0, 0, v, jj, ii) = Uf[0][0][v] - Sv;
+          R.XY(pB, 0, 1, v, jj, ii) = Uf[0][1][v] - Sv;
+          R.XY(pB, 1, 0, v, jj, ii) = Uf[1][0][v] - Sv;
+          R.XY(pB, 1, 1, v, jj, ii) = Uf[1][1][v] - Sv;
+          R.Zs(pB, 0, v, jj, ii) = Uf[2][0][v] - Sv;
+          R.Zs(pB, 1, v, jj, ii) = Uf[2][1][v] - Sv;
         }
       }
     }
-    // F: update of plane pF
-    for (int k = tid; k < nf; k += nthr) {
-      const int j = k / N, i = k - j * N;
-      T Uc[5], dF[3][5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Uc[v] = k == tid ? Un0[v] : (T)C.load_raw(v, i, j, pF);
-        dF[0][v] = R.F2x(pF, v, j, i + 1) - R.F2x(pF, v, j, i);
-        dF[1][v] = R.F2y(pF, v, j + 1, i) - R.F2y(pF, v, j, i);
-        dF[2][v] = R.F2z(pF + 1, v, j, i) - R.F2z(pF, v, j, i);
+    __syncthreads();
+
+    // ---- 2: A (next input plane) around C (3 Riemann solves per cell) -----
+    {
+      const int nx = (pB >= 0 && pB < NP) ? N * (N + 1) : 0;
+      const int ne = (pB >= 0 && pB <= NP) ? 2 * nx + N * N : 0;
+      const int na = (pA <= NP + S_) ? LW * LW : 0;
+      // load items go to the threads with the fewest face items (thread t
+      // has one face item more than the others below ne % nthr)
+      const int aw0 = ne % nthr;
+      const int naw = nthr - aw0;
+      const int atid = tid - aw0;
+      T Ua0[5];
+      if (atid >= 0 && atid < na) {
+        int jj = atid / LW, ii = atid - jj * LW;
+        C.load5(ii - 1 - S_, jj - 1 - S_, pA, Ua0);
       }
-      mark_status<N>(sts, K, pF, 0, 0, update_cell_from<T, S, MIXED, N>(C, i, j, pF, Uc, dF, o.gas));
-    }
-    // A: the read plane into the ring
-    for (int k = tid; k < na; k += nthr) {
-      const int jj = k / LW, ii = k - jj * LW;
-      T U[5], W[5];
-      if (k == tid) {
+      if (ne) stage_flux2<T, S, MIXED, RS, N>(C, o, R, pB, K, sts);
+      for (int k = atid; atid >= 0 && k < na; k += naw) {
+        int jj = k / LW, ii = k - jj * LW;
+        T U[5], W[5];
+        if (k == atid) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) U[v] = Ua0[v];
-      } else {
-        C.load5(ii - 1 - S_, jj - 1 - S_, pA, U);
+          for (int v = 0; v < 5; ++v) U[v] = Ua0[v];
+        } else {
+          C.load5(ii - 1 - S_, jj - 1 - S_, pA, U);
+        }
+        prim<T, MIXED>(U, W, o.gas);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Wr(pA, v, jj, ii) = W[v];
       }
-      prim<T, MIXED>(U, W, o.gas);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Wr(pA, v, jj, ii) = W[v];
     }
     __syncthreads();
   }

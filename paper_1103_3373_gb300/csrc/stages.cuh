@@ -19,15 +19,14 @@ namespace hyd {
 //   F2x: [var][N rows][N+1 faces]   (face f between cells f-1 and f)
 //   F2y: [var][N+1 faces][N cols]
 //   F2z: [var][N][N], the faces below plane p
-// Depths: DXY / DZ planes of face states, D2 planes of final fluxes.
-template <class T, int N, int DXY, int DZ, int D2 = 2> struct FaceRings {
+template <class T, int N, int DXY, int DZ> struct FaceRings {
   static constexpr int L = N + 2, LL = L * L;
   static constexpr int XYPL = 2 * 2 * 5 * LL;
   static constexpr int ZPL = 2 * 5 * LL;
   static constexpr int F2X = 5 * N * (N + 1);
   static constexpr int F2XYPL = 2 * F2X;
   static constexpr int F2ZPL = 5 * N * N;
-  static constexpr int ELEMS = DXY * XYPL + DZ * ZPL + D2 * F2XYPL + D2 * F2ZPL;
+  static constexpr int ELEMS = DXY * XYPL + DZ * ZPL + 2 * F2XYPL + 2 * F2ZPL;
   T* base;
   __device__ __forceinline__ T& XY(int p, int dir, int side, int v, int jj, int ii) const {
     return base[slot<DXY>(p) * XYPL + (((dir * 2 + side) * 5 + v) * L + jj) * L + ii];
@@ -36,13 +35,13 @@ template <class T, int N, int DXY, int DZ, int D2 = 2> struct FaceRings {
     return base[DXY * XYPL + slot<DZ>(p) * ZPL + ((side * 5 + v) * L + jj) * L + ii];
   }
   __device__ __forceinline__ T& F2x(int p, int v, int j, int f) const {
-    return base[DXY * XYPL + DZ * ZPL + slot<D2>(p) * F2XYPL + (v * N + j) * (N + 1) + f];
+    return base[DXY * XYPL + DZ * ZPL + slot<2>(p) * F2XYPL + (v * N + j) * (N + 1) + f];
   }
   __device__ __forceinline__ T& F2y(int p, int v, int f, int i) const {
-    return base[DXY * XYPL + DZ * ZPL + slot<D2>(p) * F2XYPL + F2X + (v * (N + 1) + f) * N + i];
+    return base[DXY * XYPL + DZ * ZPL + slot<2>(p) * F2XYPL + F2X + (v * (N + 1) + f) * N + i];
   }
   __device__ __forceinline__ T& F2z(int p, int v, int j, int i) const {
-    return base[DXY * XYPL + DZ * ZPL + D2 * F2XYPL + slot<D2>(p) * F2ZPL + (v * N + j) * N + i];
+    return base[DXY * XYPL + DZ * ZPL + 2 * F2XYPL + slot<2>(p) * F2ZPL + (v * N + j) * N + i];
   }
 };
 
