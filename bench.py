@@ -482,7 +482,11 @@ def record_traffic(csv_path, command=""):
     out = {"source_sha": source_hash(),
            "kernel": "advance_kernel<CTU,PPM,ROE,FP32,16>, 256^3 periodic box, fused gather, chained columns",
            "bytes_per_launch": launches, "bytes_per_cell": float(np.mean(launches)) / N_BOX ** 3,
-           "source_csv": os.path.basename(csv_path),
+           "command": "python bench.py --steps 20 --warmup 3 --quick --block-threads 512 > plain.log && "
+                      "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
+                      "--clock-control none -k regex:\"advance_kernel|cfl_\" --csv --log-file launches.csv "
+                      "python bench.py --steps 20 --warmup 3 --quick --block-threads 512 && "
+                      "python bench.py --record-traffic launches.csv",
            "note": "dram__bytes_read.sum + dram__bytes_write.sum per launch; valid only while source_sha matches "
                    "the headline kernel's sources"}
     with open(os.path.join(ROOT, "paper_1103_3373_gb300", "data", "ncu_traffic.json"), "w") as fh:
