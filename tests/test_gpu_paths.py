@@ -352,9 +352,19 @@ def test_cfl_dt_boxes_equals_per_box(torch_dev, prec):
     a = dt.cpu().numpy()
     assert np.isnan(a[1]) and np.isnan(a[-1])
     np.testing.assert_array_equal(np.delete(a[:-1], 1), np.delete(b, 1))
+    # the largest table: CFL_MAX_BOXES boxes in one call, each its own dt
+    many = [(Us[k % len(Us)], dxs[k % len(Us)]) for k in range(H.CFL_MAX_BOXES)]
+    dtm = torch.full((H.CFL_MAX_BOXES,), float("nan"), dtype=torch.float64, device=dev)
+    H.hydro_cfl_dt_boxes([(U, dx_, dtm[k:k + 1]) for k, (U, dx_) in enumerate(many)], 0.45, ws, precision=prec)
+    torch.cuda.synchronize()
+    a = dt.cpu().numpy()[:-1]
+    np.testing.assert_array_equal(dtm.cpu().numpy(), np.array([a[k % len(Us)] for k in range(H.CFL_MAX_BOXES)]))
     # argument errors
     with pytest.raises(H.HydroError) as e:
         H.hydro_cfl_dt_boxes([], 0.45, ws)
+    assert e.value.code == H.EINVAL
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_cfl_dt_boxes([(Us[0], dxs[0], dtm[:1])] * (H.CFL_MAX_BOXES + 1), 0.45, ws, precision=prec)
     assert e.value.code == H.EINVAL
     with pytest.raises(H.HydroError) as e:
         H.hydro_cfl_dt_boxes(boxes[:1], 0.45, ws1[:64], precision=prec)
