@@ -84,6 +84,27 @@ def test_autotune_picks_a_working_shape(small_levels):
     assert (again["block_threads"], again["grid_ctas"]) == (best["block_threads"], best["grid_ctas"])
 
 
+def test_autotune_uniform_picks_chain_length():
+    """On a uniform box the tuner also searches the chain length (the tile's
+    extent along z) and returns it; the step's bytes do not depend on it."""
+    import torch
+    from paper_1103_3373_gb300 import autotune
+    U = W.lognormal(64, seed=3, mach=1.2)
+    box = RT.UniformBox(U, _params(), cfl=0.4)
+    box.advance()
+    torch.cuda.synchronize()
+    ref = box.b.clone()
+    autotune._CACHE.clear()
+    best = box.tune()
+    assert best["chain"] in (0, 8, 4, 2)
+    assert {t[2] for t in best["tried"]} == {0, 8, 4, 2}
+    assert box.p.chain == best["chain"]
+    box.b.fill_(float("nan"))
+    box.advance()
+    torch.cuda.synchronize()
+    assert torch.equal(box.b, ref)
+
+
 def test_serving_results_same_alone_and_in_the_mix():
     import torch
     reqs = [SV.Request(rid=i, t_arrive=0.0, n=n, mach=m, steps=s, seed=sd)

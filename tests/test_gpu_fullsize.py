@@ -74,6 +74,7 @@ def test_c2_one_step_sampled_groups(box256, scheme, recon, rs, prec):
     assert np.array_equal(sts[pick] & H.ST_ERROR_MASK, ref_st & H.ST_ERROR_MASK)
     if prec == H.FP64:
         assert np.array_equal(sts[pick], ref_st)
+        np.testing.assert_array_equal(sub, ref)  # same formulas, same order: bit for bit
     assert not np.any(sts & H.ST_ERROR_MASK)
     tot0 = U.reshape(5, -1).sum(axis=1)
     tot1 = got.reshape(5, -1).sum(axis=1)

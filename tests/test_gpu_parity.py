@@ -47,6 +47,16 @@ def test_advance_matches_oracle(scheme, recon, rs, prec):
     assert np.array_equal(st & H.ST_ERROR_MASK, ref_st & H.ST_ERROR_MASK)
     if prec == H.FP64:
         assert np.array_equal(st, ref_st)
+        _fp64_bit_exact(rs, got, ref, flux, ref_flux)
+
+
+def _fp64_bit_exact(rs, got, ref, flux, ref_flux):
+    """FP64 evaluates the oracle's formulas in its operation order without
+    contraction: bit for bit equal, except where the exact solver's pow()
+    (the device library's against the host's) may differ in the last place."""
+    if rs != O.EXACT:
+        np.testing.assert_array_equal(got, ref)
+        np.testing.assert_array_equal(flux, ref_flux)
 
 
 CHAR_COMBOS = list(itertools.product([O.MHM, O.VL, O.CTU], [O.PLM, O.PPM]))
@@ -73,6 +83,7 @@ def test_characteristic_reconstruction_matches_oracle(scheme, recon, prec, j):
     assert np.array_equal(st & H.ST_ERROR_MASK, ref_st & H.ST_ERROR_MASK)
     if prec == H.FP64:
         assert np.array_equal(st, ref_st)
+        _fp64_bit_exact(rs, got, ref, flux, ref_flux)
     # and it is a different scheme from the primitive form
     ref_p = _case(scheme, recon, rs, H.FP64, limiter, theta, seed=2 + j, p_index=1.4, mach=0.7)[0]
     assert rel_l1(ref_p, ref) > 1e-3
@@ -99,6 +110,7 @@ def test_limiters_fp64(limiter, theta):
     ref, ref_flux, ref_st, got, flux, st = _case(O.CTU, O.PPM, O.ROE, H.FP64, limiter, theta, seed=4)
     assert_close(got, ref, H.FP64, "state")
     assert_close(flux, ref_flux, H.FP64, "flux", axis_var=2)
+    _fp64_bit_exact(O.ROE, got, ref, flux, ref_flux)
 
 
 @pytest.mark.parametrize("fallback", [O.HLLE, O.HLLC, O.EXACT])
