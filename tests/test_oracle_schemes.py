@@ -250,3 +250,32 @@ def test_op_count_is_positive_and_deterministic():
     b, cb = O.count_ops(P, Ug[0], N)
     assert a == b and ca == cb
     assert a["riemann"]["add"] > 0 and a["trace"]["mul"] > 0 and a["correct"]["add"] > 0
+
+
+@pytest.mark.slow
+def test_sedov_taylor_radius_and_spherical_symmetry():
+    """Sedov-Taylor blast (E = 1 in r < 2 cells, rho = 1, p = 1e-5, gamma = 5/3;
+    CTU + PPM + HLLC, outflow, 48^3): the shock radius, taken from the density
+    maximum along the six axis rays, follows the self-similar closed form
+    R(t) = xi0 (E t^2 / rho)^(1/5), xi0 = 1.15 for gamma = 5/3, within one cell
+    width at R = 0.2 and 0.3; the six rays are the same profile (the blast
+    sits on the cube's centre, so every axis is equivalent) to roundoff."""
+    from tests.oracle_runs import oracle_run
+    n, xi0 = 48, 1.15
+    U = W.sedov(n)
+    P = O.Params(scheme=O.CTU, recon=O.PPM, riemann=O.HLLC, limiter=O.MINMOD, theta=1.0, fallback=O.HLLE,
+                 gamma=5.0 / 3.0, dens_floor=1e-12, pres_floor=1e-12, dt=0.0, dx=(1.0 / n,) * 3)
+    t = 0.0
+    for R in (0.2, 0.3):
+        t_end = (R / xi0) ** 2.5  # E = rho = 1
+        U, dt_t, st = oracle_run(U, P, 16, 3, 1, 100000, cfl=0.4, t_end=t_end - t)
+        t += dt_t
+        assert st & O.ST_ERROR_MASK == 0
+        assert t == pytest.approx(t_end, rel=1e-12)
+        rho, c = U[0], n // 2
+        rays = [rho[c, c, c:], rho[c, c, :c][::-1], rho[c, c:, c], rho[c, :c, c][::-1], rho[c:, c, c],
+                rho[:c, c, c][::-1]]
+        for r in rays[1:]:
+            np.testing.assert_allclose(r, rays[0], rtol=0, atol=1e-12)
+        R_num = (np.argmax(rays[0]) + 0.5) / n
+        assert abs(R_num - xi0 * t ** 0.4) <= 1.0 / n, (R, R_num)
