@@ -166,6 +166,17 @@ template <class T, class S, int N> struct GroupCtx {
       for (int v = 0; v < 5; ++v) U[v] = (T)p[v * XYZ];
     }
   }
+  // Address of variable 0 at (x, y, z) (ghost zone allowed, box edges
+  // wrapped or clamped as in load5) and the stride between variables.
+  __device__ __forceinline__ const S* src5(int x, int y, int z, long long& vstride) const {
+    if (mode == 0) {
+      vstride = Mpl * M;
+      return in + ((long long)(z + g) * M + (y + g)) * M + (x + g);
+    }
+    int sx = wrap(ox + x, X, bc), sy = wrap(oy + y, Y, bc), sz = wrap(oz + z, Z, bc);
+    vstride = XYZ;
+    return in + ((long long)sz * Y + sy) * X + sx;
+  }
   __device__ __forceinline__ S load_raw(int v, int x, int y, int z) const {
     if (mode == 0) return in[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
     return in[v * XYZ + ((long long)(oz + z) * Y + (oy + y)) * X + (ox + x)];

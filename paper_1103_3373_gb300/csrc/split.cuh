@@ -12,6 +12,8 @@
 // [0, N) along the first sweep's axis, the last [0, N)^2; the fluxes through
 // the group faces of each sweep's update are the boundary fluxes (step (5)).
 #pragma once
+#include <cuda_pipeline.h>
+
 #include "stages.cuh"
 
 namespace hyd {
@@ -255,16 +257,14 @@ __device__ __forceinline__ void waf_row(T* p, int sd, const LocalComps& lc, cons
   }
 }
 
-template <class T, class S, bool MIXED, int SCH, int LIM, int N>
-__device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
-                                                 unsigned* sts) {
-  constexpr int G = SplitGhost<SCH>::value;
-  constexpr int M = N + 2 * G;
+// The padded group into a global-memory ring (FP64 forms): UB cells per
+// thread are loaded before any of them is stored, so their global reads are
+// in flight together.
+template <class T, class S, bool MIXED, int G, int M, int N>
+__device__ __forceinline__ void split_load_group(const GroupCtx<T, S, N>& C, T* ring) {
   constexpr int M2 = M * M, M3 = M * M * M;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  // the padded group into the ring: UB cells per thread are loaded before
-  // any of them is stored, so their global reads are in flight together
   constexpr int UB = (sizeof(T) == 4 && !MIXED) ? 2 : 1;
+  const int tid = threadIdx.x, nthr = blockDim.x;
   for (int base = tid; base < M3; base += UB * nthr) {
     T U[UB][5];
 #pragma unroll
@@ -284,6 +284,31 @@ __device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N>& C, con
       }
     }
   }
+}
+
+template <class T, class S, bool MIXED, int SCH, int LIM, int N>
+__device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
+                                                 unsigned* sts) {
+  constexpr int G = SplitGhost<SCH>::value;
+  constexpr int M = N + 2 * G;
+  constexpr int M2 = M * M, M3 = M * M * M;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if constexpr (sizeof(T) == 4 && sizeof(S) == 4) {
+    // the padded group into the shared-memory ring with asynchronous
+    // global-to-shared copies: every copy of the thread is in flight at
+    // once, nothing is staged in registers
+    for (int idx = tid; idx < M3; idx += nthr) {
+      const int z = idx / M2, r = idx - z * M2, y = r / M, x = r - y * M;
+      long long vs;
+      const S* src = C.src5(x - G, y - G, z - G, vs);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) __pipeline_memcpy_async(&ring[v * M3 + idx], src + v * vs, sizeof(T));
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+  } else {
+    split_load_group<T, S, MIXED, G, M, N>(C, ring);
+  }
   __syncthreads();
   const int first = o.split_order ? 2 : 0, last = o.split_order ? 0 : 2;
   for (int k = 0; k < 3; ++k) {
@@ -298,7 +323,9 @@ __device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N>& C, con
     const int s1 = e1 == 0 ? 1 : M;
     const int s2 = e2 == 1 ? M : M2;
     const LocalComps lc(d);
-    const T dtdx = C.dtdx[d], hdtdx = C.hdtdx[d];
+    // selects, not an index: a run-time index would put the context in local memory
+    const T dtdx = d == 0 ? C.dtdx[0] : (d == 1 ? C.dtdx[1] : C.dtdx[2]);
+    const T hdtdx = d == 0 ? C.hdtdx[0] : (d == 1 ? C.hdtdx[1] : C.hdtdx[2]);
     for (int r = tid; r < n1 * n2; r += nthr) {
       const int q2 = r / n1, q1 = r - q2 * n1;
       const int c1 = q1 + o1, c2 = q2 + o2;  // padded coordinates
