@@ -28,6 +28,8 @@
 // states on the cells [-1,N] along their normal and [0,N-1] laterally;
 // stage-2 fluxes on the faces of the interior cells.
 #pragma once
+#include <cuda_pipeline.h>
+
 #include "stages.cuh"
 
 namespace hyd {
@@ -229,12 +231,31 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
       const int pa = q + 1 + S_;  // plane the next tracing needs last
       const int na = (pa <= NP + S_) ? LW * LW : 0;
       // the next plane's global loads are issued first and converted after
-      // the Riemann work, so their latency hides behind it
-      // the load items go to the threads with the fewest face items: thread t
-      // has ceil((ne - t) / nthr) of them, one more below ne % nthr
+      // the Riemann work, so their latency hides behind it.  FP32 forms: as
+      // asynchronous global-to-shared copies of the conserved values straight
+      // into the plane's ring slot (that of plane q-S, which the tracing has
+      // finished with), every copy in flight at once; each thread converts
+      // the cells it copied, in place, once its own copies have landed.
+      // FP64 (ring in global memory): the load items go to the threads with
+      // the fewest face items (thread t has ceil((ne - t) / nthr) of them,
+      // one more below ne % nthr), their first cell's reads issued first.
+      constexpr bool ASYNC = sizeof(T) == 4 && sizeof(S) == 4;
+      // copies (and their conversions) go to the threads with the fewest
+      // face items when there are enough of them, else to all threads
+      const int cw0 = ASYNC && 4 * (nthr - ne % nthr) >= nthr ? ne % nthr : 0;
+      if constexpr (ASYNC) {
+        for (int k = tid - cw0; k >= 0 && k < na; k += nthr - cw0) {
+          const int jj = k / LW, ii = k - jj * LW;
+          long long vs;
+          const S* src = C.src5(ii - 1 - S_, jj - 1 - S_, pa, vs);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) __pipeline_memcpy_async(&Wr(pa, v, jj, ii), src + v * vs, sizeof(T));
+        }
+        __pipeline_commit();
+      }
       const int aw0 = ne % nthr;
       const int naw = nthr - aw0;
-      const int atid = tid - aw0;
+      const int atid = ASYNC ? -1 : tid - aw0;
       T Ua0[5];
       if (atid >= 0 && atid < na) {
         int jj = atid / LW, ii = atid - jj * LW;
@@ -359,6 +380,18 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
         prim<T, MIXED>(U, W, o.gas);
 #pragma unroll
         for (int v = 0; v < 5; ++v) Wr(pa, v, jj, ii) = W[v];
+      }
+      if constexpr (ASYNC) {
+        __pipeline_wait_prior(0);
+        for (int k = tid - cw0; k >= 0 && k < na; k += nthr - cw0) {
+          const int jj = k / LW, ii = k - jj * LW;
+          T U[5], W[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) U[v] = Wr(pa, v, jj, ii);
+          prim<T, MIXED>(U, W, o.gas);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Wr(pa, v, jj, ii) = W[v];
+        }
       }
     }
     __syncthreads();

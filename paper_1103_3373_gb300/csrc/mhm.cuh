@@ -19,6 +19,8 @@
 //      A  then converted to primitives and stored in the ring (in the slot
 //         of plane pB-S, which B has finished with).
 #pragma once
+#include <cuda_pipeline.h>
+
 #include "stages.cuh"
 
 namespace hyd {
@@ -130,11 +132,30 @@ __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
       const int nx = (pB >= 0 && pB < NP) ? N * (N + 1) : 0;
       const int ne = (pB >= 0 && pB <= NP) ? 2 * nx + N * N : 0;
       const int na = (pA <= NP + S_) ? LW * LW : 0;
-      // load items go to the threads with the fewest face items (thread t
-      // has one face item more than the others below ne % nthr)
+      // FP32 forms: the conserved values of plane pA go straight into its
+      // ring slot (that of plane pB-S, which B has finished with) by
+      // asynchronous global-to-shared copies, all in flight during C; each
+      // thread converts the cells it copied, in place, after its own copies
+      // have landed.  FP64 (ring in global memory): load items go to the
+      // threads with the fewest face items (thread t has one face item more
+      // than the others below ne % nthr).
+      constexpr bool ASYNC = sizeof(T) == 4 && sizeof(S) == 4;
+      // copies (and their conversions) go to the threads with the fewest
+      // face items when there are enough of them, else to all threads
+      const int cw0 = ASYNC && 4 * (nthr - ne % nthr) >= nthr ? ne % nthr : 0;
+      if constexpr (ASYNC) {
+        for (int k = tid - cw0; k >= 0 && k < na; k += nthr - cw0) {
+          const int jj = k / LW, ii = k - jj * LW;
+          long long vs;
+          const S* src = C.src5(ii - 1 - S_, jj - 1 - S_, pA, vs);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) __pipeline_memcpy_async(&Wr(pA, v, jj, ii), src + v * vs, sizeof(T));
+        }
+        __pipeline_commit();
+      }
       const int aw0 = ne % nthr;
       const int naw = nthr - aw0;
-      const int atid = tid - aw0;
+      const int atid = ASYNC ? -1 : tid - aw0;
       T Ua0[5];
       if (atid >= 0 && atid < na) {
         int jj = atid / LW, ii = atid - jj * LW;
@@ -153,6 +174,18 @@ __device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
         prim<T, MIXED>(U, W, o.gas);
 #pragma unroll
         for (int v = 0; v < 5; ++v) Wr(pA, v, jj, ii) = W[v];
+      }
+      if constexpr (ASYNC) {
+        __pipeline_wait_prior(0);
+        for (int k = tid - cw0; k >= 0 && k < na; k += nthr - cw0) {
+          const int jj = k / LW, ii = k - jj * LW;
+          T U[5], W[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) U[v] = Wr(pA, v, jj, ii);
+          prim<T, MIXED>(U, W, o.gas);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Wr(pA, v, jj, ii) = W[v];
+        }
       }
     }
     __syncthreads();

@@ -22,6 +22,8 @@
 // streams through a chain of K groups stacked along z (planes 0..KN-1)
 // without restarting.
 #pragma once
+#include <cuda_pipeline.h>
+
 #include "stages.cuh"
 
 namespace hyd {
@@ -213,10 +215,25 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
       const int nxE = (d >= 0 && d < NP) ? N * (N + 1) : 0;
       const int cntE = (d >= 0 && d <= NP) ? 2 * nxE + N * N : 0;
       const int ne = cntC + cntE;
-      // load items go to the threads with the fewest C/E items
+      // FP32 forms: plane a goes straight into its ring slot (the slot of
+      // plane a-3, which nothing reads any more) by asynchronous global-to-
+      // shared copies, all in flight while C and E run.  FP64 (rings in
+      // global memory): load items go to the threads with the fewest C/E
+      // items, their first cell's reads issued before C and E.
+      constexpr bool ASYNC = sizeof(T) == 4 && sizeof(S) == 4;
+      if constexpr (ASYNC) {
+        for (int k = tid; k < na; k += nthr) {
+          const int jj = k / LU, ii = k - jj * LU;
+          long long vs;
+          const S* src = C.src5(ii - 2 - S_, jj - 2 - S_, a, vs);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) __pipeline_memcpy_async(&Ur(a, v, jj, ii), src + v * vs, sizeof(T));
+        }
+        __pipeline_commit();
+      }
       const int aw0 = ne % nthr;
       const int naw = nthr - aw0;
-      const int atid = tid - aw0;
+      const int atid = ASYNC ? -1 : tid - aw0;
       T Ua0[5];
       if (atid >= 0 && atid < na) {
         int jj = atid / LU, ii = atid - jj * LU;
@@ -253,6 +270,7 @@ __device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, 
 #pragma unroll
         for (int v = 0; v < 5; ++v) Ur(a, v, jj, ii) = U[v];
       }
+      if constexpr (ASYNC) __pipeline_wait_prior(0);
     }
     __syncthreads();
   }
