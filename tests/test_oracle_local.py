@@ -240,6 +240,29 @@ def test_trace_ppm_single_wave_subsonic_mixed_signs(u):
             np.testing.assert_allclose(Wl, want_l, rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("u", [0.3, -0.3, 0.0])
+def test_trace_plm_single_wave_both_edges_mixed_signs(u):
+    """PLM analogue of the PPM single-wave pin: a slope along one right
+    eigenvector of numpy's primitive Jacobian is transported by its own speed
+    to the edge it travels to, W0 +- (1 -+ lambda_k dt/dx) dW / 2; the other
+    edge keeps the reference state of the fastest wave towards it."""
+    g = 1.4
+    W0 = np.array([1.2, u, -0.15, 0.25, 1.0])
+    A = prim_jacobian(W0, g)
+    lam, R = np.linalg.eig(A)
+    lam, R = lam.real, R.real
+    c = np.sqrt(g * W0[4] / W0[0])
+    dtdx = 0.35
+    lM, lm = max(u + c, 0.0), min(u - c, 0.0)
+    for k in range(5):
+        dW = 0.02 * R[:, k]
+        Wl, Wr = O.trace(O.PLM, W0, dW, None, dtdx, g)
+        lr = lam[k] if lam[k] > 0 else lM
+        ll = lam[k] if lam[k] < 0 else lm
+        np.testing.assert_allclose(Wr, W0 + 0.5 * (1 - lr * dtdx) * dW, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(Wl, W0 - 0.5 * (1 + ll * dtdx) * dW, rtol=1e-12, atol=1e-15)
+
+
 def test_trace_ppm_superposition_of_waves():
     # the tracing is linear in (dA, W6) for frozen eigenvectors: two waves of
     # opposite signs together equal the sum of their separate corrections
