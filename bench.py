@@ -22,6 +22,7 @@ For N > 1 (torchrun, one rank per GPU) every rank advances its own box
 (independent replicas: weak scaling, no collective on the data path).
 """
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -208,7 +209,8 @@ def amr_leg(H, RT, W, torch, dev, steps=20):
     (refined where |grad rho|/rho > 0.3 on a seeded 128^3 lognormal root), per-
     level dx and device dt.  FP32 batched persistent launch replayed from a
     CUDA graph and autotuned, against the same FP32 step as one launch per
-    level and the plain FP64 per-level launch."""
+    level, the same batched launch with every group advanced alone, and the
+    plain FP64 per-level launch (groups alone)."""
     t = time.perf_counter()
     levels = W.amr_levels()
     gen_s = time.perf_counter() - t
@@ -230,7 +232,22 @@ def amr_leg(H, RT, W, torch, dev, steps=20):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     out["fp32_batched_graph"] = {"value": cells / (ms / 1e3), "ms_per_step": ms,
-                                 "block_threads": tb["block_threads"]}
+                                 "block_threads": tb["block_threads"], "chain": tb["chain"],
+                                 "runs": "z-continuations streamed as chains (zrun)"}
+    # the same launch shape with every group advanced alone
+    lb1 = RT.LevelBatch(levels, dataclasses.replace(lb.p, chain=1), cfl=CFL, device=dev, chains=False)
+    lb1.capture()
+    for _ in range(3):
+        lb1.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(steps):
+        lb1.replay()
+    b.record()
+    torch.cuda.synchronize()
+    ms1 = a.elapsed_time(b) / steps
+    out["fp32_batched_graph_groups_alone"] = {"value": cells / (ms1 / 1e3), "ms_per_step": ms1}
+    del lb1
     for _ in range(2):
         lb.step_per_level()
     torch.cuda.synchronize()
@@ -243,7 +260,7 @@ def amr_leg(H, RT, W, torch, dev, steps=20):
     out["fp32_per_level"] = {"value": cells / (ms / 1e3), "ms_per_step": ms}
     del lb
     torch.cuda.empty_cache()
-    lb = RT.LevelBatch(levels, make_params(H, H.FP64, (1.0, 1.0, 1.0)), cfl=CFL, device=dev)
+    lb = RT.LevelBatch(levels, make_params(H, H.FP64, (1.0, 1.0, 1.0)), cfl=CFL, device=dev, chains=False)
     lb.step_per_level()
     torch.cuda.synchronize()
     a.record()

@@ -116,6 +116,24 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge
  *                one, so CTAs on neighbouring columns pass the same layers
  *                at about the same time and share their halo planes in L2.
  *                Results do not depend on it (the autotuner picks it).
+ *                For prepared groups with zrun it caps the runs a CTA
+ *                streams through (0 = HYDRO_CHAIN_MAX).
+ *   zrun         prepared groups (hydro_advance; hydro_level.zrun for
+ *                hydro_advance_levels): device int[G] or NULL.  zrun[g] >= 1
+ *                is the number of groups g, g+1, ... each of which continues
+ *                the one before it along +z: its interior lies directly
+ *                above, and the ghost zones of the two hold each other's
+ *                interior values (as a gather or the AMR ghost preparation
+ *                from one level makes them).  A CTA then streams through up
+ *                to `chain` such groups without restarting, reading the
+ *                planes between them from the interiors.  Values are
+ *                clamped to [1, groups left in the entry]; NULL = every
+ *                group alone.  Used by the CTU kernels (the other schemes
+ *                advance every group alone): a launch with runs runs a
+ *                variant of the kernel, whose results equal byte for byte
+ *                those of the same launch with runs of one (every group
+ *                alone), and those of a launch without runs to rounding
+ *                (FP64 byte for byte).
  *
  * The split schemes (the directionally split comparison schemes of Sec.
  * 3.2): RTVD = relaxing TVD in the flux-split form of Trac & Pen (2003),
@@ -136,6 +154,7 @@ typedef struct hydro_params {
   int characteristic;
   int split_order;
   int chain;
+  const int* zrun;
 } hydro_params;
 
 /* Ghost layers the scheme needs (Sec. 2): MHM and CTU 2 (PLM) / 3 (PPM);
@@ -220,6 +239,8 @@ typedef struct hydro_level {
   int G;                /* groups (mode 0); ignored in mode 1 (derived from X, Y, Z)  */
   int mode;             /* 0 = prepared groups, 1 = uniform field with bc             */
   int bc, X, Y, Z;      /* mode 1 only                                                */
+  const int* zrun;      /* mode 0: device int[G] runs of z-continuations, or NULL
+                           (as hydro_params.zrun)                                    */
 } hydro_level;
 
 /* Most entries one hydro_advance_levels call accepts. */

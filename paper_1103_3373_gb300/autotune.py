@@ -12,7 +12,9 @@ and keeps the fastest:
     extent along z: how many z-consecutive 16^3 groups a CTA streams through
     without restarting, 1 .. CHAIN_MAX; the work list then runs in
     z-segments of that many layers), so the tile shape is tuned between one
-    group (16^3) and a whole column (16^2 x 16 K).
+    group (16^3) and a whole column (16^2 x 16 K); for prepared groups given
+    with runs of z-continuations (an AMR level's columns, a refined group's
+    z-pairs), the longest chain through those runs.
 The tile's lateral extent (16^2, one patch group) and the ghost width are
 not candidates: the lateral extent is set by the shared-memory rings of a
 group's planes (the CTU rings take 220 KB of the 227 KB a CTA may hold, so a
@@ -41,11 +43,17 @@ def _key(p: H.Params, tag):
 
 
 def chain_candidates(p: H.Params, tag):
-    """Chain lengths worth timing: only uniform fields of the unsplit schemes
-    chain (0 = whole columns, up to CHAIN_MAX)."""
-    if tag != "uniform" or p.scheme > H.CTU:
+    """Chain lengths worth timing: uniform fields of the unsplit schemes
+    (0 = whole columns, up to CHAIN_MAX), and prepared groups given with
+    runs of z-continuations (tag "levels_runs", the CTU kernels; 0 = whole
+    runs, 1 = every group alone).  Other work does not chain."""
+    if p.scheme > H.CTU:
         return [p.chain]
-    return [0, 8, 4, 2]
+    if tag == "uniform":
+        return [0, 8, 4, 2]
+    if tag == "levels_runs" and p.scheme == H.CTU:
+        return [0, 4, 2, 1]
+    return [p.chain]
 
 
 def _load_file():

@@ -110,8 +110,8 @@ template <class T> __device__ __forceinline__ T correct(T u, T h1, T a1p, T a1m,
   return u;
 }
 
-template <class T, class S, bool MIXED, int RS, int REC, int LIM, bool CH, int N>
-__device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K,
+template <class T, class S, bool MIXED, int RS, int REC, int LIM, bool CH, int N, bool GCH>
+__device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* ring, int K,
                                                unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = CtuLayout<N, S_>;
@@ -398,8 +398,8 @@ __device__ __forceinline__ void ctu_group_impl(const GroupCtx<T, S, N>& C, const
   }
 }
 
-template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N>
-__device__ void ctu_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
+template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N, bool GCH>
+__device__ void ctu_group(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   if (o.limiter == LIM_MINMOD && o.theta == T(1))
     ctu_group_impl<T, S, MIXED, RS, REC, LIM_MINMOD1, CH, N>(C, o, ring, K, sts);
   else

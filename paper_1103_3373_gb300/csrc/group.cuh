@@ -19,7 +19,8 @@ struct SegDesc {
   double dx[3];
   int G, mode, bc, X, Y, Z, GX, GY, GZ;
   int gz0;              // mode 1: first group layer of the entry (its GZ layers follow)
-  int lc;               // mode 1: z-segment length of the work order (1..CHAIN_MAX)
+  int lc;               // mode 1: z-segment length of the work order; mode 0: longest chain (1..CHAIN_MAX)
+  const int* zrun;      // mode 0: [G] groups from g on that continue one another along z, or null
   int first;            // flat index of this entry's first group
 };
 
@@ -82,13 +83,14 @@ struct KConst {
 // z-neighbours.  The user's group index (flux and status arrays) is
 // x-fastest:
 //   gu = gx + GX (gy + GY gz).
-template <class T, class S, int N> struct GroupCtx {
+template <class T, class S, int N, bool GCH = false> struct GroupCtx {
   const S* in;
   S* out;
   S* flux;            // boundary fluxes of the chain's first group
   long long fstride;  // elements between the flux arrays of chain groups
   int gu, ustride;    // user index of the first group; step between chain groups
   int mode, bc, g, M;
+  int kmax;  // mode 0: last group of the chain (K - 1)
   long long Mpl;  // M*M
   int X, Y, Z, ox, oy, oz;
   long long XYZ;
@@ -96,8 +98,9 @@ template <class T, class S, int N> struct GroupCtx {
 
   // sc[0..2] = dt/dx_d, sc[3..5] = (0.5 dt)/dx_d, evaluated once per group
   // (group_consts) and shared by the CTA.
-  __device__ __forceinline__ void init(const SegDesc& sg, int gi, const KConst& kc, const double* sc) {
+  __device__ __forceinline__ void init(const SegDesc& sg, int gi, const KConst& kc, const double* sc, int K = 1) {
     mode = sg.mode;
+    kmax = K - 1;
     g = kc.ghost;
     M = N + 2 * g;
     Mpl = (long long)M * M;
@@ -146,17 +149,37 @@ template <class T, class S, int N> struct GroupCtx {
     return a < 0 ? 0 : (a >= n ? n - 1 : a);
   }
 
+  // Mode 0 chains (GCH: kernels that stream gathered groups as chains): plane
+  // z of a chain of K gathered groups (z-consecutive, ghost zones agreeing
+  // with each other's interiors) is read from group k = clamp(floor(z / N),
+  // 0, K-1) at its local plane z - kN, so the planes between two groups come
+  // from interiors and the ghost planes only from the first group's bottom
+  // and the last group's top.  The group's input array starts at
+  // in + 5 M^3 k; on return z is the local plane.  Without GCH every chain
+  // is one group and the array is in.
+  __device__ __forceinline__ const S* gin(int& z) const {
+    if constexpr (!GCH) return in;
+    int k = z < 0 ? 0 : z / N;
+    k = k < kmax ? k : kmax;
+    z -= k * N;
+    return in + (long long)k * 5 * Mpl * M;
+  }
+
   // Input value of variable v at interior coordinates (x, y, z), which may lie
   // in the ghost zone (-g <= x < N + g).
   __device__ __forceinline__ T load(int v, int x, int y, int z) const {
-    if (mode == 0) return (T)in[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
+    if (mode == 0) {
+      const S* b = gin(z);
+      return (T)b[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
+    }
     int sx = wrap(ox + x, X, bc), sy = wrap(oy + y, Y, bc), sz = wrap(oz + z, Z, bc);
     return (T)in[v * XYZ + ((long long)sz * Y + sy) * X + sx];
   }
   // All five variables at (x, y, z) (ghost zone allowed).
   __device__ __forceinline__ void load5(int x, int y, int z, T U[5]) const {
     if (mode == 0) {
-      const S* p = in + ((long long)(z + g) * M + (y + g)) * M + (x + g);
+      const S* p = gin(z);
+      p += ((long long)(z + g) * M + (y + g)) * M + (x + g);
 #pragma unroll
       for (int v = 0; v < 5; ++v) U[v] = (T)p[v * Mpl * M];
     } else {
@@ -171,21 +194,29 @@ template <class T, class S, int N> struct GroupCtx {
   __device__ __forceinline__ const S* src5(int x, int y, int z, long long& vstride) const {
     if (mode == 0) {
       vstride = Mpl * M;
-      return in + ((long long)(z + g) * M + (y + g)) * M + (x + g);
+      const S* b = gin(z);
+      return b + ((long long)(z + g) * M + (y + g)) * M + (x + g);
     }
     int sx = wrap(ox + x, X, bc), sy = wrap(oy + y, Y, bc), sz = wrap(oz + z, Z, bc);
     vstride = XYZ;
     return in + ((long long)sz * Y + sy) * X + sx;
   }
+  // Interior values (0 <= z < K N).
   __device__ __forceinline__ S load_raw(int v, int x, int y, int z) const {
-    if (mode == 0) return in[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
+    if (mode == 0) {
+      const S* b = gin(z);
+      return b[v * Mpl * M + ((long long)(z + g) * M + (y + g)) * M + (x + g)];
+    }
     return in[v * XYZ + ((long long)(oz + z) * Y + (oy + y)) * X + (ox + x)];
   }
   __device__ __forceinline__ void store(int v, int x, int y, int z, S val) const {
-    if (mode == 0)
-      out[(long long)v * N * N * N + (z * N + y) * N + x] = val;
-    else
+    if (mode == 0) {
+      const int k = GCH ? z / N : 0;
+      z -= k * N;
+      out[(long long)(5 * k + v) * N * N * N + (z * N + y) * N + x] = val;
+    } else {
       out[v * XYZ + ((long long)(oz + z) * Y + (oy + y)) * X + (ox + x)] = val;
+    }
   }
   // Boundary flux of face f (0..5) of chain group k at transverse indices
   // (a, b).
@@ -228,8 +259,8 @@ template <class T> __device__ __forceinline__ unsigned state_status(const T Un[5
 // evaluated in the arithmetic type for every form: the result is rounded to
 // the storage type, so an FP64 sum would change the stored FP32 value by less
 // than one unit in the last place.
-template <class T, class S, bool MIXED, int N>
-__device__ __forceinline__ unsigned update_cell_from(const GroupCtx<T, S, N>& C, int x, int y, int z, const T U0[5],
+template <class T, class S, bool MIXED, int N, bool GCH>
+__device__ __forceinline__ unsigned update_cell_from(const GroupCtx<T, S, N, GCH>& C, int x, int y, int z, const T U0[5],
                                                      const T dF[3][5], const Gas<T>& gas) {
   T Un[5];
 #pragma unroll
@@ -257,8 +288,8 @@ template <class T> __device__ __forceinline__ unsigned state_status(const T Un[5
   return st;
 }
 
-template <class T, class S, bool MIXED, int N>
-__device__ __forceinline__ unsigned update_cell(const GroupCtx<T, S, N>& C, int x, int y, int z, const T dF[3][5],
+template <class T, class S, bool MIXED, int N, bool GCH>
+__device__ __forceinline__ unsigned update_cell(const GroupCtx<T, S, N, GCH>& C, int x, int y, int z, const T dF[3][5],
                                                 const Gas<T>& gas) {
   T U0[5];
 #pragma unroll

@@ -36,7 +36,7 @@ struct State {
   KernelEntry tab[NKEY];
   int nsm[MAX_DEV] = {0};
   int smem_optin[MAX_DEV] = {0};
-  bool attr_set[MAX_DEV][NKEY] = {{false}};
+  bool attr_set[MAX_DEV][NKEY][2] = {{{false}}};  // [.][.][RUNS variant]
   int occ[MAX_DEV][NKEY][3] = {{{0}}};  // cached occupancy per block size class
 };
 
@@ -123,12 +123,13 @@ bool valid_physics(const hydro_params* p) {
 // Resolved launch of one configuration on the current device.
 struct Launch {
   const KernelEntry* k;
+  const void* fn;  // the kernel: k->fn, or k->fn_runs for launches with runs of gathered groups
   int dev, key, threads, grid;
   size_t smem_bytes;
   size_t ws_bytes;
 };
 
-int resolve(const hydro_params* p, int N, long long total_groups, Launch& L) {
+int resolve(const hydro_params* p, int N, long long total_groups, Launch& L, bool runs = false) {
   if (!p) return HYDRO_EINVAL;
   if (!valid_enums(p)) return HYDRO_EINVAL;
   if (N != 16) return HYDRO_EUNSUPPORTED;
@@ -142,20 +143,22 @@ int resolve(const hydro_params* p, int N, long long total_groups, Launch& L) {
   L.key = kernel_key(p->scheme, p->recon, p->characteristic, p->riemann, p->precision);
   L.k = &s.tab[L.key];
   if (!L.k->fn) return HYDRO_EUNSUPPORTED;
+  const bool rv = runs && L.k->fn_runs;
+  L.fn = rv ? L.k->fn_runs : L.k->fn;
   int maxt = L.k->max_threads;
   L.threads = p->block_threads ? p->block_threads : maxt;
   if (L.threads < 32 || L.threads > maxt || (L.threads & 31)) return HYDRO_EINVAL;
   L.smem_bytes = L.k->smem ? (size_t)L.k->ring_elems * L.k->elem_bytes : 0;
   if (L.k->smem && (int)L.smem_bytes > s.smem_optin[L.dev]) return HYDRO_EUNSUPPORTED;
-  if (!s.attr_set[L.dev][L.key]) {
+  if (!s.attr_set[L.dev][L.key][rv]) {
     if (L.k->smem) {
-      cudaError_t e = cudaFuncSetAttribute(L.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+      cudaError_t e = cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
       if (e != cudaSuccess) return cuda_fail(e);
     }
-    s.attr_set[L.dev][L.key] = true;
+    s.attr_set[L.dev][L.key][rv] = true;
   }
   int occ = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.k->fn, L.threads, L.smem_bytes);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, L.threads, L.smem_bytes);
   if (e != cudaSuccess) return cuda_fail(e);
   if (occ < 1) return HYDRO_EUNSUPPORTED;
   long long g = p->grid_ctas > 0 ? p->grid_ctas : (long long)nsm * occ;
@@ -170,7 +173,9 @@ int resolve(const hydro_params* p, int N, long long total_groups, Launch& L) {
 
 int launch_table(const hydro_params* p, const WorkTable& wt, int N, int ghost, void* stream) {
   Launch L;
-  int rc = resolve(p, N, wt.total, L);
+  bool runs = false;  // an entry of gathered groups with runs of z-continuations
+  for (int s = 0; s < wt.nseg; ++s) runs = runs || (wt.seg[s].mode == 0 && wt.seg[s].zrun);
+  int rc = resolve(p, N, wt.total, L, runs);
   if (rc) return rc;
   if (wt.total == 0) return HYDRO_OK;
   if (!L.k->smem) {
@@ -188,7 +193,7 @@ int launch_table(const hydro_params* p, const WorkTable& wt, int N, int ghost, v
   kc.ring_elems = L.k->ring_elems;
   void* ws = p->workspace;
   void* args[] = {(void*)&wt, (void*)&kc, (void*)&ws};
-  cudaError_t e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.threads), args, L.smem_bytes, (cudaStream_t)stream);
+  cudaError_t e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.threads), args, L.smem_bytes, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e);
   return HYDRO_OK;
 }
@@ -267,6 +272,8 @@ int hydro_advance(const hydro_params* p, const void* U_in, void* U_out, void* fl
   for (int d = 0; d < 3; ++d) s.dx[d] = p->dx[d];
   s.G = G;
   s.mode = 0;
+  s.zrun = p->zrun;
+  s.lc = p->chain > 0 ? p->chain : CHAIN_MAX;
   s.first = 0;
   return launch_table(p, wt, N, ghost, stream);
 }
@@ -378,6 +385,8 @@ int hydro_advance_levels(const hydro_params* p, const hydro_level* levels, int n
     if (lv.mode == 0) {
       if (lv.G < 0) return HYDRO_EINVAL;
       G = lv.G;
+      s.zrun = lv.zrun;
+      s.lc = p->chain > 0 ? p->chain : CHAIN_MAX;
     } else {
       if (lv.X <= 0 || lv.Y <= 0 || lv.Z <= 0 || lv.X % N || lv.Y % N || lv.Z % N) return HYDRO_EINVAL;
       if (lv.bc != HYDRO_BC_PERIODIC && lv.bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;

@@ -33,13 +33,18 @@ template <int PR, int RS, int SCH = 0> struct MaxThreads {
   static constexpr int value = PR == P_FP64 ? 256 : ((RS == RS_EXACT || SCH >= SCH_RTVD) ? 384 : 512);
 };
 
-template <int SCH, int REC, int RS, int PR, int N, bool CH>
+// RUNS: the variant that also streams runs of gathered groups as chains
+// (hydro_params.zrun; CTU only).  It is a kernel of its own so that the code
+// of the other forms stays as it is; every form of one launch runs the same
+// compiled copy, so they give the same bytes.
+template <int SCH, int REC, int RS, int PR, int N, bool CH, bool RUNS = false>
 __global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
     advance_kernel(const __grid_constant__ WorkTable wt, const KConst kc, void* ws) {
   using Tr = KTraits<SCH, REC, PR, N>;
   using T = typename Tr::T;
   using S = typename Tr::S;
   constexpr bool MIXED = Tr::P::MIXED;
+  constexpr bool GCH = RUNS && SCH <= CTU;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned sts[CHAIN_MAX];  // status of the groups of the current chain
   __shared__ double sc[6];
@@ -73,11 +78,21 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
       const int left = seg_pos(sg, gi).left;  // groups left in this z-segment
       K = wend - w < left ? wend - w : left;
       K = K < CHAIN_MAX ? K : CHAIN_MAX;
+    } else if (GCH && sg.zrun) {
+      // gathered groups: the run of z-continuations starting here, cut at
+      // the CTA's share, the entry's end and the chain limit
+      int left = sg.zrun[gi];
+      left = left < sg.G - gi ? left : sg.G - gi;
+      left = left < sg.lc ? left : sg.lc;
+      K = wend - w < left ? wend - w : left;
+      K = K > 1 ? K : 1;
     }
     if (threadIdx.x == 0) group_consts(sg, sc);
     __syncthreads();
-    GroupCtx<T, S, N> C;
-    C.init(sg, gi, kc, sc);
+    // one compiled copy of the group pipeline serves every form of an entry,
+    // so that all forms give the same bytes
+    GroupCtx<T, S, N, GCH> C;
+    C.init(sg, gi, kc, sc, K);
     if constexpr (SCH == CTU)
       ctu_group<T, S, MIXED, RS, REC, CH, N>(C, o, ring, K, sts);
     else if constexpr (SCH == MHM)
@@ -98,6 +113,7 @@ __global__ void __launch_bounds__(MaxThreads<PR, RS, SCH>::value, 1)
 // Host-side description of one compiled kernel.
 struct KernelEntry {
   const void* fn;
+  const void* fn_runs;  // the RUNS variant, or null
   long long ring_elems;
   int elem_bytes;
   int max_threads;
@@ -114,6 +130,7 @@ template <int SCH, int REC, int RS, int PR, int N, bool CH> inline void put_kern
   using Tr = KTraits<SCH, REC, PR, N>;
   KernelEntry& e = tab[kernel_key(SCH, REC, CH ? 1 : 0, RS, PR)];
   e.fn = (const void*)&advance_kernel<SCH, REC, RS, PR, N, CH>;
+  if constexpr (SCH == CTU) e.fn_runs = (const void*)&advance_kernel<SCH, REC, RS, PR, N, CH, true>;
   e.ring_elems = Tr::RING;
   e.elem_bytes = (int)sizeof(typename Tr::T);
   e.max_threads = MaxThreads<PR, RS, SCH>::value;

@@ -84,8 +84,8 @@ __device__ __forceinline__ void mhm_faces(const WRing& Wr, int p, int jj, int ii
   }
 }
 
-template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N>
-__device__ void mhm_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
+template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N, bool GCH>
+__device__ void mhm_group(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = MhmLayout<N, S_>;
   constexpr int L = Lay::L, LL = L * L, LW = Lay::LW;

@@ -260,8 +260,8 @@ __device__ __forceinline__ void waf_row(T* p, int sd, const LocalComps& lc, cons
 // The padded group into a global-memory ring (FP64 forms): UB cells per
 // thread are loaded before any of them is stored, so their global reads are
 // in flight together.
-template <class T, class S, bool MIXED, int G, int M, int N>
-__device__ __forceinline__ void split_load_group(const GroupCtx<T, S, N>& C, T* ring) {
+template <class T, class S, bool MIXED, int G, int M, int N, bool GCH>
+__device__ __forceinline__ void split_load_group(const GroupCtx<T, S, N, GCH>& C, T* ring) {
   constexpr int M2 = M * M, M3 = M * M * M;
   constexpr int UB = (sizeof(T) == 4 && !MIXED) ? 2 : 1;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -286,8 +286,8 @@ __device__ __forceinline__ void split_load_group(const GroupCtx<T, S, N>& C, T* 
   }
 }
 
-template <class T, class S, bool MIXED, int SCH, int LIM, int N>
-__device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring,
+template <class T, class S, bool MIXED, int SCH, int LIM, int N, bool GCH>
+__device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* ring,
                                                  unsigned* sts) {
   constexpr int G = SplitGhost<SCH>::value;
   constexpr int M = N + 2 * G;
@@ -360,8 +360,8 @@ __device__ __forceinline__ void split_group_impl(const GroupCtx<T, S, N>& C, con
   }
 }
 
-template <class T, class S, bool MIXED, int SCH, int N>
-__device__ void split_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, unsigned* sts) {
+template <class T, class S, bool MIXED, int SCH, int N, bool GCH>
+__device__ void split_group(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* ring, unsigned* sts) {
   if (o.limiter == LIM_MINMOD && o.theta == T(1))
     split_group_impl<T, S, MIXED, SCH, LIM_MINMOD1, N>(C, o, ring, sts);
   else

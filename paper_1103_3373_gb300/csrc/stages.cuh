@@ -51,8 +51,8 @@ template <class T, int N, int DXY, int DZ> struct FaceRings {
 // p-1 and p.  Fluxes on a group boundary are stored at once (step (5)); a z
 // face between two groups of a chain is the +z face of the lower and the -z
 // face of the upper one.
-template <class T, class S, bool MIXED, int RS, int N, class FR>
-__device__ __forceinline__ void flux2_item(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+template <class T, class S, bool MIXED, int RS, int N, class FR, bool GCH>
+__device__ __forceinline__ void flux2_item(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, const FR& R, int p, int K,
                                            unsigned* sts, int idx, int nx) {
   constexpr int LL = FR::LL;
   const int pk = p / N;  // chain group of plane p (K for the top face)
@@ -120,8 +120,8 @@ __device__ __forceinline__ void flux2_item(const GroupCtx<T, S, N>& C, const Opt
 }
 
 // All final Riemann solves of chain plane p, over the CTA's threads.
-template <class T, class S, bool MIXED, int RS, int N, class FR>
-__device__ __forceinline__ void stage_flux2(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+template <class T, class S, bool MIXED, int RS, int N, class FR, bool GCH>
+__device__ __forceinline__ void stage_flux2(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, const FR& R, int p, int K,
                                             unsigned* sts) {
   const int nx = (p < K * N) ? N * (N + 1) : 0;
   const int cnt = 2 * nx + N * N;
@@ -130,8 +130,8 @@ __device__ __forceinline__ void stage_flux2(const GroupCtx<T, S, N>& C, const Op
 
 // Conservative update of cell idx (of N^2) of chain plane p from the final
 // fluxes (step (4)).
-template <class T, class S, bool MIXED, int N, class FR>
-__device__ __forceinline__ void update_item(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+template <class T, class S, bool MIXED, int N, class FR, bool GCH>
+__device__ __forceinline__ void update_item(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, const FR& R, int p, int K,
                                             unsigned* sts, int idx) {
   int j = idx / N, i = idx - j * N;
   T dF[3][5];
@@ -145,8 +145,8 @@ __device__ __forceinline__ void update_item(const GroupCtx<T, S, N>& C, const Op
 }
 
 // Conservative update of chain plane p, over the CTA's threads.
-template <class T, class S, bool MIXED, int N, class FR>
-__device__ __forceinline__ void stage_update(const GroupCtx<T, S, N>& C, const Opts<T>& o, const FR& R, int p, int K,
+template <class T, class S, bool MIXED, int N, class FR, bool GCH>
+__device__ __forceinline__ void stage_update(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, const FR& R, int p, int K,
                                              unsigned* sts) {
   for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) update_item<T, S, MIXED, N>(C, o, R, p, K, sts, idx);
 }
@@ -163,8 +163,8 @@ template <class T, int LW, int R> struct PlaneRing {
 };
 
 // Load plane p into a ring, as primitives (PRIM) or conserved variables.
-template <bool PRIM, class T, class S, bool MIXED, int N, int LW, int R>
-__device__ __forceinline__ void stage_load(const GroupCtx<T, S, N>& C, const Opts<T>& o, int p, int off,
+template <bool PRIM, class T, class S, bool MIXED, int N, int LW, int R, bool GCH>
+__device__ __forceinline__ void stage_load(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, int p, int off,
                                            const PlaneRing<T, LW, R>& ring) {
   for (int idx = threadIdx.x; idx < LW * LW; idx += blockDim.x) {
     int jj = idx / LW, ii = idx - jj * LW;

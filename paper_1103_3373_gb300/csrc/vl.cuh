@@ -127,8 +127,8 @@ __device__ __forceinline__ void vl_recon_item(const WRing& Wh, const FR& R, int 
   }
 }
 
-template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N>
-__device__ void vl_group(const GroupCtx<T, S, N>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
+template <class T, class S, bool MIXED, int RS, int REC, bool CH, int N, bool GCH>
+__device__ void vl_group(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* ring, int K, unsigned* sts) {
   constexpr int S_ = REC == PPM ? 2 : 1;
   using Lay = VlLayout<N, S_>;
   constexpr int L = Lay::L, LH = Lay::LH, LU = Lay::LU;

@@ -50,14 +50,15 @@ class _CParams(ctypes.Structure):
                 ("dx", ctypes.c_double * 3), ("dens_floor", ctypes.c_double), ("pres_floor", ctypes.c_double),
                 ("dt_dev", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("characteristic", ctypes.c_int), ("split_order", ctypes.c_int), ("chain", ctypes.c_int)]
+                ("characteristic", ctypes.c_int), ("split_order", ctypes.c_int), ("chain", ctypes.c_int),
+                ("zrun", ctypes.c_void_p)]
 
 
 class _CLevel(ctypes.Structure):
     _fields_ = [("U_in", ctypes.c_void_p), ("U_out", ctypes.c_void_p), ("flux", ctypes.c_void_p),
                 ("status", ctypes.c_void_p), ("dt_dev", ctypes.c_void_p), ("dt", ctypes.c_double),
                 ("dx", ctypes.c_double * 3), ("G", ctypes.c_int), ("mode", ctypes.c_int), ("bc", ctypes.c_int),
-                ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int)]
+                ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int), ("zrun", ctypes.c_void_p)]
 
 
 class _CAmrLevel(ctypes.Structure):
@@ -87,6 +88,7 @@ class Params:
     characteristic: int = 0  # 1: PLM / PPM on characteristic variables (Sec. 2)
     split_order: int = 0     # RTVD / WAF: sweeps x, y, z (0) or z, y, x (1)
     chain: int = 0           # uniform fields: z-segment / chain length (0 = whole columns, <= CHAIN_MAX)
+    zrun: object = None      # prepared groups: device int32 [G] runs of z-continuations (zrun_of)
 
     def c(self):
         p = _CParams()
@@ -98,6 +100,7 @@ class Params:
         for d in range(3):
             p.dx[d] = float(self.dx[d])
         p.dt_dev = _ptr(self.dt_dev, "dt_dev", dtype="float64") if self.dt_dev is not None else None
+        p.zrun = _ptr(self.zrun, "zrun", dtype="int32") if self.zrun is not None else None
         if self.workspace is not None:
             p.workspace = self.workspace.data_ptr()
             p.workspace_bytes = self.workspace.numel() * self.workspace.element_size()
@@ -325,6 +328,7 @@ class Level:
     status: object = None
     mode: int = 0
     bc: int = BC_PERIODIC
+    zrun: object = None  # mode 0: device int32 [G] runs of z-continuations (hydro_params.zrun)
 
 
 def make_levels(levels, precision):
@@ -343,6 +347,7 @@ def make_levels(levels, precision):
         c.mode = int(lv.mode)
         if lv.mode == 0:
             c.G = lv.U_in.shape[0]
+            c.zrun = _ptr(lv.zrun, "zrun", "int32") if lv.zrun is not None else None
         else:
             c.bc = int(lv.bc)
             _, c.Z, c.Y, c.X = (int(s) for s in lv.U_in.shape)

@@ -185,11 +185,13 @@ class LevelBatch:
     step() = one CFL reduction per level + the batched launch; it takes no
     host synchronisation and can be captured once into a CUDA graph
     (capture()) and replayed.  step_per_level() is the plain form: one
-    hydro_advance launch per level.
+    hydro_advance launch per level.  A level dict may carry `zrun` (runs of
+    groups that continue one another along z, hydro_params.zrun): both forms
+    then stream through those runs (chains=False ignores them).
     """
 
     def __init__(self, levels, params: H.Params, cfl=0.4, N=16, ghost=3, device="cuda:0", stream=None,
-                 store_flux=True):
+                 store_flux=True, chains=True):
         torch = _torch()
         self.torch = torch
         self.dev = torch.device(device)
@@ -198,7 +200,10 @@ class LevelBatch:
         self.N, self.ghost = N, ghost
         dt = torch.float64 if params.precision == H.FP64 else torch.float32
         self.U_in, self.U_out, self.flux, self.status, self.dts, self.dx = [], [], [], [], [], []
+        self.zrun = []
         for lv in levels:
+            zr = lv.get("zrun") if chains else None
+            self.zrun.append(torch.as_tensor(np.asarray(zr, dtype=np.int32)).to(self.dev) if zr is not None else None)
             U = torch.as_tensor(lv["U"], dtype=dt).to(self.dev).contiguous()
             G = U.shape[0]
             self.U_in.append(U)
@@ -208,6 +213,8 @@ class LevelBatch:
             self.dts.append(torch.zeros(1, dtype=torch.float64, device=self.dev))
             self.dx.append((lv["dx"],) * 3)
         self.cells = sum(u.shape[0] for u in self.U_in) * N ** 3
+        # autotuner cache tag: chain lengths are candidates only with runs
+        self.tune_tag = "levels_runs" if any(z is not None for z in self.zrun) else "levels"
         self.red_ws = torch.empty(H.hydro_cfl_boxes_workspace_bytes(), dtype=torch.uint8, device=self.dev)
         self.cfl_boxes = H.make_cfl_boxes([(self.U_in[l], self.dx[l], self.dts[l]) for l in range(len(self.U_in))],
                                           params.precision)
@@ -219,7 +226,8 @@ class LevelBatch:
         nws = H.hydro_workspace_bytes(self.p, self.N)
         self.p.workspace = self.torch.empty(nws, dtype=self.torch.uint8, device=self.dev) if nws else None
         self.entries = [H.Level(U_in=self.U_in[l], U_out=self.U_out[l], flux=self.flux[l], status=self.status[l],
-                                dx=self.dx[l], dt_dev=self.dts[l], mode=0) for l in range(len(self.U_in))]
+                                dx=self.dx[l], dt_dev=self.dts[l], mode=0, zrun=self.zrun[l])
+                        for l in range(len(self.U_in))]
         self.carray = H.make_levels(self.entries, self.p.precision)
 
     def reduce_dt(self, stream=None):
@@ -240,17 +248,17 @@ class LevelBatch:
         s = stream if stream is not None else self.stream
         self.reduce_dt(s)
         for l in range(len(self.U_in)):
-            self.p.dx, self.p.dt_dev = self.dx[l], self.dts[l]
+            self.p.dx, self.p.dt_dev, self.p.zrun = self.dx[l], self.dts[l], self.zrun[l]
             H.hydro_advance(self.p, self.U_in[l], self.U_out[l], self.flux[l], self.status[l], N=self.N,
                             ghost=self.ghost, stream=s)
-        self.p.dt_dev = None
+        self.p.dt_dev, self.p.zrun = None, None
 
     def tune(self, verbose=False):
         from . import autotune
         self.torch.cuda.synchronize()
         best = autotune.tune(self.p, lambda p: H.hydro_advance_levels(
             p, self.entries, N=self.N, ghost=self.ghost, stream=None,
-            _carray=H.make_levels(self.entries, p.precision)), tag="levels", verbose=verbose)
+            _carray=H.make_levels(self.entries, p.precision)), tag=self.tune_tag, verbose=verbose)
         self._alloc_ws()
         return best
 

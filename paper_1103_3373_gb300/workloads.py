@@ -147,6 +147,24 @@ def group_origins(X, Y, Z, N=16):
     return np.asarray(o, dtype=np.int32).reshape(-1, 3)
 
 
+def column_origins(X, Y, Z, N=16):
+    """The origins of group_origins in column order: z fastest, then x, then
+    y, so that z-neighbouring groups are consecutive."""
+    o = [(gx * N, gy * N, gz * N) for gy in range(Y // N) for gx in range(X // N) for gz in range(Z // N)]
+    return np.asarray(o, dtype=np.int32).reshape(-1, 3)
+
+
+def runs_from_links(nxt):
+    """zrun[g] = 1 + zrun[g+1] where group g+1 continues group g along +z
+    (nxt[g] true), else 1: the run of z-continuations starting at g."""
+    nxt = np.asarray(nxt, dtype=bool)
+    z = np.ones(len(nxt), dtype=np.int32)
+    for g in range(len(nxt) - 2, -1, -1):
+        if nxt[g]:
+            z[g] = z[g + 1] + 1
+    return z
+
+
 def scatter_groups(U_groups, X, Y, Z):
     """Inverse of the interior tiling: [G,5,N,N,N] -> [5,Z,Y,X]."""
     G, _, N = U_groups.shape[:3]
@@ -192,7 +210,10 @@ def amr_levels(counts=(4096, 2500, 1500, 800), n0=128, seed=5, N=16, g=3, mach=1
     trilinear interpolation of the parent's halo-padded data, with a seeded
     1% k^-3 density perturbation.  Ghost zones are prepared (filled from the
     parent), as the AMR ghost interpolation itself is not part of this path.
-    Returns a list of dicts {U: groups, dx, score, flagged_fraction}.
+    Groups that continue one another along z are consecutive: level 0 column
+    by column (z fastest) within each shifted root, the children of a refined
+    group as four z-pairs; `zrun` gives the runs (hydro_params.zrun).
+    Returns a list of dicts {U: groups, dx, score, flagged_fraction, zrun}.
     """
     from scipy import ndimage
     rng = np.random.default_rng(seed)
@@ -200,44 +221,49 @@ def amr_levels(counts=(4096, 2500, 1500, 800), n0=128, seed=5, N=16, g=3, mach=1
     M = N + 2 * g
     levels = []
     # level 0
-    groups, scores = [], []
+    groups, scores, nxt = [], [], []
     shift = np.zeros(3, dtype=int)
     while len(groups) < counts[0]:
         f = np.roll(root, tuple(-shift[::-1]), axis=(1, 2, 3))
         fp = _pad_periodic(f, g)
         sc = _grad_score(fp[0])
-        for (x0, y0, z0) in group_origins(n0, n0, n0, N):
+        for (x0, y0, z0) in column_origins(n0, n0, n0, N):
             if len(groups) >= counts[0]:
                 break
             groups.append(fp[:, z0:z0 + M, y0:y0 + M, x0:x0 + M])
             scores.append(sc[z0:z0 + M - 2, y0:y0 + M - 2, x0:x0 + M - 2].max())
+            nxt.append(z0 + N < n0)  # the next group of this root's column lies above
         shift = rng.integers(0, n0, 3)
     U0 = np.stack(groups).astype(dtype)
     levels.append({"U": U0, "dx": 1.0 / n0, "score": np.asarray(scores),
-                   "flagged_fraction": float(np.mean(np.asarray(scores) > threshold))})
+                   "flagged_fraction": float(np.mean(np.asarray(scores) > threshold)),
+                   "zrun": runs_from_links(nxt[:len(groups) - 1] + [False])})
     # refined levels
     for l in range(1, len(counts)):
         prev = levels[-1]
         need = int(np.ceil(counts[l] / 8))
         order = np.argsort(-prev["score"], kind="stable")
         parents = [order[k % len(order)] for k in range(need)]
-        kids, ksc = [], []
+        kids, ksc, nxt = [], [], []
         for pi in parents:
             P = prev["U"][pi].astype(np.float64)
             fine = np.stack([ndimage.zoom(P[v], 2, order=1, mode="nearest", grid_mode=True) for v in range(5)])
             pert = gaussian_field(2 * M, int(rng.integers(0, 2 ** 31 - 1)))
             fine[0] *= 1.0 + 0.01 * pert
             sc = _grad_score(fine[0])
-            for cz in (0, 1):
-                for cy in (0, 1):
-                    for cx in (0, 1):
+            for cy in (0, 1):
+                for cx in (0, 1):
+                    for cz in (0, 1):
                         a = (N * cz + 2 * g - g, N * cy + 2 * g - g, N * cx + 2 * g - g)
                         kids.append(fine[:, a[0]:a[0] + M, a[1]:a[1] + M, a[2]:a[2] + M])
                         ksc.append(sc[a[0]:a[0] + M - 2, a[1]:a[1] + M - 2, a[2]:a[2] + M - 2].max())
-        Ul = np.stack(kids[:counts[l]]).astype(dtype)
-        sl = np.asarray(ksc[:counts[l]])
+                        nxt.append(cz == 0)  # the upper child of the pair follows
+        G = counts[l]
+        Ul = np.stack(kids[:G]).astype(dtype)
+        sl = np.asarray(ksc[:G])
         levels.append({"U": Ul, "dx": prev["dx"] / 2.0, "score": sl,
-                       "flagged_fraction": float(np.mean(sl > threshold))})
+                       "flagged_fraction": float(np.mean(sl > threshold)),
+                       "zrun": runs_from_links(nxt[:G - 1] + [False])})
     return levels
 
 

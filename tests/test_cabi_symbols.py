@@ -86,6 +86,29 @@ def test_binding_marshals_its_structs():
     assert [f[0] for f in H._CAmrLevel._fields_] == ["U", "origin", "map", "G", "X", "Y", "Z"]
 
 
+def _header_struct_fields(src, name):
+    """Field names of `typedef struct name { ... } name;` in declaration order."""
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            names.append(re.sub(r"\[.*\]", "", part).replace("*", " ").split()[-1])
+    return names
+
+
+def test_binding_structs_follow_the_header():
+    """The ctypes mirrors of hydro_params and hydro_level list the header's
+    fields in the header's order."""
+    from paper_1103_3373_gb300 import hydro as H
+    src = open(os.path.join(ROOT, "include", "hydro.h")).read()
+    assert _header_struct_fields(src, "hydro_params") == [f[0] for f in H._CParams._fields_]
+    assert _header_struct_fields(src, "hydro_level") == [f[0] for f in H._CLevel._fields_]
+
+
 def test_python_constants_match_the_header():
     """Sizes the binding copies from include/hydro.h (the no-allocation
     entry point's scratch limit, the level-table size) are the header's."""

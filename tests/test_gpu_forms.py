@@ -4,6 +4,8 @@
   launch equal one launch per level byte for byte; the CUDA-graph replay of a
   step equals the eager step; sampled groups of every level match the oracle
   with that level's dx and dt.
+* Prepared groups in runs of z-continuations stream as chains with the
+  bytes of every group advanced alone.
 * Autotuner: picks a launch shape that runs and gives the same bytes.
 * Serving: every request's result is the same alone and in the mix (and
   equal to stepping its box on its own with UniformBox).
@@ -66,6 +68,63 @@ def test_levels_batched_graph_and_oracle(small_levels):
         assert_close(fl[l][pick].double().cpu().numpy(), ref_flux, H.FP32, "level %d flux" % l, axis_var=2)
 
 
+@pytest.mark.parametrize("prec", [H.FP64, H.FP32, H.FP32_MIXED])
+@pytest.mark.parametrize("scheme,recon,rs", [(H.CTU, H.PPM, H.RS_ROE), (H.CTU, H.PLM, H.RS_HLLC),
+                                             (H.VL, H.PLM, H.RS_HLLC)])
+def test_levels_runs_equal_groups_alone(small_levels, prec, scheme, recon, rs):
+    """Prepared groups given with runs of z-continuations (zrun: a level's
+    columns, a refined group's z-pairs) stream through each run as one chain
+    in the CTU kernels (VL ignores the runs).  State, boundary fluxes and
+    status equal, byte for byte, those of every group advanced alone (runs
+    of one: the same kernel, which launches with runs use), for every chain
+    limit and grid (grids of 7 and 3 CTAs give each CTA several groups, so
+    runs become chains, cut at other places) and per level as in the batched
+    launch.  Without runs the groups go through the plain kernel; that
+    equals the runs of one to the tolerance of the parity tests."""
+    import torch
+    assert max(int(lv["zrun"].max()) for lv in small_levels) >= 2
+    ones = [dict(lv, zrun=np.ones_like(lv["zrun"])) for lv in small_levels]
+
+    def batch(levels, chains=True):
+        p = H.Params(scheme=scheme, recon=recon, riemann=rs, precision=prec, dens_floor=1e-6, pres_floor=1e-6)
+        assert H.hydro_required_ghost(scheme, recon) <= 3  # the workload's groups carry 3 ghost layers
+        return RT.LevelBatch(levels, p, ghost=3, chains=chains)
+
+    def snap(lb):
+        torch.cuda.synchronize()
+        return ([u.clone() for u in lb.U_out], [f.clone() for f in lb.flux], [s.clone() for s in lb.status])
+
+    def reset(lb):
+        for u, f, s in zip(lb.U_out, lb.flux, lb.status):
+            u.fill_(float("nan"))
+            f.fill_(float("nan"))
+            s.fill_(-1)
+
+    alone = batch(ones)
+    alone.step()
+    ref = snap(alone)
+    plain = batch(small_levels, chains=False)
+    plain.step()
+    for a, b in zip(snap(plain)[0], ref[0]):
+        assert_close(a.double().cpu().numpy(), b.double().cpu().numpy(), prec, "plain kernel vs runs of one")
+    lb = batch(small_levels)
+    for grid, chain in ((0, 0), (0, 1), (0, 2), (7, 0), (3, 3)):
+        lb.p.grid_ctas, lb.p.chain = grid, chain
+        lb._alloc_ws()
+        reset(lb)
+        lb.step()
+        got = snap(lb)
+        for a, b in zip(ref, got):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y), (grid, chain)
+    reset(lb)
+    lb.step_per_level()
+    got = snap(lb)
+    for a, b in zip(ref, got):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+
+
 def test_autotune_picks_a_working_shape(small_levels):
     import torch
     from paper_1103_3373_gb300 import autotune
@@ -80,7 +139,7 @@ def test_autotune_picks_a_working_shape(small_levels):
     for a, b in zip(ref, lb.U_out):
         assert torch.equal(a, b)
     # cached: a second call returns the same choice without re-timing
-    again = autotune.tune(lb.p, lambda p: None, tag="levels")
+    again = autotune.tune(lb.p, lambda p: None, tag=lb.tune_tag)
     assert (again["block_threads"], again["grid_ctas"]) == (best["block_threads"], best["grid_ctas"])
 
 
