@@ -304,13 +304,28 @@ def amr_hierarchy_leg(H, RT, W, torch, dev, replays=10):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / (2 * replays)
-    out["fp32_graph"] = {"value": hier.cells_per_step / (ms / 1e3), "ms_per_step": ms, "steps": 2 * replays}
+    out["fp32_graph"] = {"value": hier.cells_per_step / (ms / 1e3), "ms_per_step": ms, "steps": 2 * replays,
+                         "runs": "each level's columns streamed as chains (zrun)"}
     tot = sum(split.values())
     out["eager_split_ms"] = {k: round(v, 3) for k, v in split.items()}
     out["eager_split_share"] = {k: round(v / tot, 4) for k, v in split.items()}
     out["errors"] = hier.errors()
     out["state_finite"] = bool(all(torch.isfinite(u).all().item() for u in hier.cur))
     out["unit"] = UNIT
+    del hier
+    torch.cuda.empty_cache()
+    # the same hierarchy with every group advanced alone
+    hier = RT.AmrHierarchy(levels, make_params(H, H.FP32, (1.0, 1.0, 1.0)), device=dev, chains=False)
+    hier.capture(dt0)
+    hier.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(replays):
+        hier.replay()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / (2 * replays)
+    out["fp32_graph_groups_alone"] = {"value": hier.cells_per_step / (ms / 1e3), "ms_per_step": ms}
     del hier
     torch.cuda.empty_cache()
     return out

@@ -283,6 +283,19 @@ def _no_timer(kind):
     return _NoTimer()
 
 
+def zrun_of(origin, N=16):
+    """Runs of z-continuations of a list of group origins (host int [G][3]):
+    zrun[g] = 1 + zrun[g+1] when group g+1 lies directly above group g, else
+    1 (hydro_params.zrun).  Groups of one level whose ghost zones are filled
+    from that level hold each other's interiors, as the runs require."""
+    o = np.asarray(origin, dtype=np.int64).reshape(-1, 3)
+    z = np.ones(len(o), dtype=np.int32)
+    for g in range(len(o) - 2, -1, -1):
+        if o[g + 1, 0] == o[g, 0] and o[g + 1, 1] == o[g, 1] and o[g + 1, 2] == o[g, 2] + N:
+            z[g] = z[g + 1] + 1
+    return z
+
+
 class AmrHierarchy:
     """A static AMR hierarchy resident on the GPU (level 0 covers the box,
     level l+1 refines whole level-l groups as octets; dx_l = dx_0 / 2^l),
@@ -301,9 +314,12 @@ class AmrHierarchy:
     No host synchronisation inside step(), so a step can be captured into a
     CUDA graph (capture()/replay()).  `levels` is a list of dicts {U
     [G][5][N][N][N], origin [G][3], box, dx} (workloads.amr_hierarchy).
+    Groups of a level listed in runs of z-neighbours (zrun_of) are advanced
+    as chains (chains=False: every group alone).
     """
 
-    def __init__(self, levels, params: H.Params, bc=H.BC_PERIODIC, N=16, device="cuda:0", stream=None):
+    def __init__(self, levels, params: H.Params, bc=H.BC_PERIODIC, N=16, device="cuda:0", stream=None,
+                 chains=True):
         import dataclasses
         torch = _torch()
         self.torch = torch
@@ -334,6 +350,8 @@ class AmrHierarchy:
             p = dataclasses.replace(params)
             p.dx = tuple(float(a) for a in lv["dx"])
             p.dt_dev = None
+            zr = zrun_of(lv["origin"], N)
+            p.zrun = torch.as_tensor(zr).to(self.dev) if chains and zr.max() > 1 else None
             self.params.append(p)
         nws = H.hydro_workspace_bytes(self.params[0], N)
         ws = torch.empty(nws, dtype=torch.uint8, device=self.dev) if nws else None

@@ -313,10 +313,11 @@ def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0,
     8) eligible level-l groups nearest to `center` instead of using radii.  The data of
     every level are smooth_field sampled at that level's cell centres, so
     coarse and fine data are independent samples (not averages) of one field.
-    Group order: level 0 x-fastest; level l+1 octet by octet in parent order,
-    children (dz, dy, dx) lexicographic."""
+    Group order, every level: column by column (y, then x, then z fastest),
+    so that the z-neighbours of a column are consecutive (the runs of
+    z-continuations that the CTU kernels stream as chains)."""
     levels = []
-    origin = group_origins(n0, n0, n0, N)
+    origin = column_origins(n0, n0, n0, N)
     nref = len(counts) if counts is not None else len(radii)
     for l in range(nref + 1):
         n = n0 * 2 ** l
@@ -352,6 +353,7 @@ def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0,
             if not kids:
                 break
             origin = np.asarray(kids, dtype=np.int32).reshape(-1, 3)
+            origin = origin[np.lexsort((origin[:, 2], origin[:, 0], origin[:, 1]))]
         r = (np.arange(N) + 0.5) / n
         U = np.empty((len(origin), 5, N, N, N))
         for k, (x0, y0, z0) in enumerate(origin):

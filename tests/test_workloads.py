@@ -5,6 +5,7 @@ hold each other's interiors in their ghost planes (the property under which
 a chain of prepared groups reproduces the groups advanced alone)."""
 import numpy as np
 
+from paper_1103_3373_gb300 import runtime as RT
 from paper_1103_3373_gb300 import workloads as W
 
 
@@ -42,3 +43,18 @@ def test_amr_batch_runs_link_matching_ghost_planes():
                     a, b = U[k], U[k + 1]
                     assert np.array_equal(a[:, N + g:N + 2 * g], b[:, g:2 * g])  # top ghosts = interior above
                     assert np.array_equal(a[:, N:N + g], b[:, 0:g])              # bottom ghosts of the upper one
+
+
+def test_hierarchy_levels_run_by_column():
+    """Every level of the hierarchy workload lists its groups column by column,
+    so runtime.zrun_of finds runs of z-neighbours; zrun_of itself follows the
+    definition on a hand-made list."""
+    o = np.asarray([(0, 0, 0), (0, 0, 16), (0, 0, 32), (16, 0, 0), (16, 0, 32), (16, 0, 48)], dtype=np.int32)
+    assert list(RT.zrun_of(o)) == [3, 2, 1, 1, 2, 1]
+    assert list(RT.zrun_of(o[:0])) == []
+    for lv in W.amr_hierarchy(64, (0.3, 0.12)):
+        o = lv["origin"]
+        key = [(y, x, z) for x, y, z in o]
+        assert key == sorted(key)
+        z = RT.zrun_of(o)
+        assert z.max() >= 2 and z[-1] == 1
