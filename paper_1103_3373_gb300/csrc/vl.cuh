@@ -239,24 +239,25 @@ __device__ void vl_group(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* r
         int jj = atid / LU, ii = atid - jj * LU;
         C.load5(ii - 2 - S_, jj - 2 - S_, a, Ua0);
       }
-      for (int idx = tid; idx < ne; idx += nthr) {
-        if (idx < cntC) {
-          // unsplit half step of plane c, U^{n+1/2} = U^n - S, then primitives
-          int jj = idx / LH, ii = idx - jj * LH;
-          T Uh[5], W[5];
+      // the final solves first, on all threads; the half-step items then go
+      // to the threads with one solve fewer (from cntE % nthr on) when those
+      // can take them at 3 a thread, else to all threads
+      for (int idx = tid; idx < cntE; idx += nthr) flux2_item<T, S, MIXED, RS, N>(C, o, R, d, K, sts, idx, nxE);
+      const int cw = 3 * (nthr - cntE % nthr) >= cntC ? cntE % nthr : 0;
+      for (int idx = tid - cw; idx >= 0 && idx < cntC; idx += nthr - cw) {
+        // unsplit half step of plane c, U^{n+1/2} = U^n - S, then primitives
+        int jj = idx / LH, ii = idx - jj * LH;
+        T Uh[5], W[5];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            T Sv = h0 * (F1.x(c, v, jj, ii + 1) - F1.x(c, v, jj, ii)) +
-                   h1 * (F1.y(c, v, jj + 1, ii) - F1.y(c, v, jj, ii)) +
-                   h2 * (F1.z(c + 1, v, jj, ii) - F1.z(c, v, jj, ii));
-            Uh[v] = Ur(c, v, jj + 1, ii + 1) - Sv;
-          }
-          prim<T, MIXED>(Uh, W, o.gas);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) Wh(c, v, jj, ii) = W[v];
-        } else {
-          flux2_item<T, S, MIXED, RS, N>(C, o, R, d, K, sts, idx - cntC, nxE);
+        for (int v = 0; v < 5; ++v) {
+          T Sv = h0 * (F1.x(c, v, jj, ii + 1) - F1.x(c, v, jj, ii)) +
+                 h1 * (F1.y(c, v, jj + 1, ii) - F1.y(c, v, jj, ii)) +
+                 h2 * (F1.z(c + 1, v, jj, ii) - F1.z(c, v, jj, ii));
+          Uh[v] = Ur(c, v, jj + 1, ii + 1) - Sv;
         }
+        prim<T, MIXED>(Uh, W, o.gas);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Wh(c, v, jj, ii) = W[v];
       }
       for (int k = atid; atid >= 0 && k < na; k += naw) {
         int jj = k / LU, ii = k - jj * LU;
