@@ -48,6 +48,18 @@ CONFIG = {"workload": "uniform 256^3 periodic box as 4096 16^3-cell patch groups
           "l2": "no flush: the 335 MB FP32 state (671 MB FP64) exceeds the 129 MB L2 and is streamed every step"}
 
 
+def mach_distribution(U, gamma=1.4):
+    """Per-cell Mach number |v| / c of a conserved state [5][Z][Y][X] (host,
+    FP64): the input's distribution, reported beside the workload."""
+    rho = U[0].astype(np.float64)
+    v2 = (U[1].astype(np.float64) ** 2 + U[2].astype(np.float64) ** 2 + U[3].astype(np.float64) ** 2) / rho ** 2
+    p = (gamma - 1.0) * (U[4].astype(np.float64) - 0.5 * rho * v2)
+    m = np.sqrt(v2 / (gamma * p / rho))
+    q = np.percentile(m, [5, 50, 95])
+    return {"rms": float(np.sqrt((m ** 2).mean())), "p05": float(q[0]), "p50": float(q[1]), "p95": float(q[2]),
+            "max": float(m.max()), "supersonic_fraction": float((m > 1.0).mean())}
+
+
 def sm_peak_fp32_tflops(nsm, sm_mhz):
     """Nominal FP32 ALU peak (context only): SMs x 128 FP32 lanes x 2 flop per
     FMA x clock."""
@@ -561,8 +573,8 @@ def reference_arm(args, rank, world):
     sample = "each step: one CTU+PPM+Roe FP64 oracle step of the first %d of the 4096 patch groups" % S
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
-            "impl": "reference",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(CONFIG, mach=mach_distribution(U)), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -792,7 +804,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(CONFIG, parallelism="replicas%d" % world if world > 1 else "single GPU"),
+                "config": dict(CONFIG, mach=mach_distribution(U)),
+                "parallelism": "replicas%d" % world if world > 1 else "single GPU",
                 "p50_step_ms": RT.percentile(step_ms, 50), "p99_step_ms": RT.percentile(step_ms, 99),
                 "step_latency_samples": len(step_ms),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
