@@ -104,7 +104,14 @@ __device__ void mhm_group(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, T* 
     const int pF = pB - 2;
     const int pA = pB + S_ + 1;
     // ---- 1: F (update of plane pF) and B (prediction of plane pB) ---------
-    if (pF >= 0 && pF < NP) stage_update<T, S, MIXED, N>(C, o, R, pF, K, sts);
+    // the update items (whose reads of U^n wait on global memory) go to the
+    // whole warps after the prediction items when there are at least two
+    // such warps, so no warp does both; else to all threads
+    {
+      const int fw0 = (LL + 31) & ~31;
+      const int t0 = (pB <= NP && nthr - fw0 >= 64) ? fw0 : 0;
+      if (pF >= 0 && pF < NP) stage_update<T, S, MIXED, N>(C, o, R, pF, K, sts, t0);
+    }
     if (pB <= NP) {
       for (int idx = tid; idx < LL; idx += nthr) {
         int jj = idx / L, ii = idx - jj * L;

@@ -147,8 +147,11 @@ __device__ __forceinline__ void update_item(const GroupCtx<T, S, N, GCH>& C, con
 // Conservative update of chain plane p, over the CTA's threads.
 template <class T, class S, bool MIXED, int N, class FR, bool GCH>
 __device__ __forceinline__ void stage_update(const GroupCtx<T, S, N, GCH>& C, const Opts<T>& o, const FR& R, int p, int K,
-                                             unsigned* sts) {
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) update_item<T, S, MIXED, N>(C, o, R, p, K, sts, idx);
+                                             unsigned* sts, int t0 = 0) {
+  // on the threads t0 .. blockDim.x-1
+  const int step = (int)blockDim.x - t0;
+  for (int idx = (int)threadIdx.x - t0; idx >= 0 && idx < N * N; idx += step)
+    update_item<T, S, MIXED, N>(C, o, R, p, K, sts, idx);
 }
 
 // Ring of LW x LW input planes; the plane's lateral index ii maps to the
