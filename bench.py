@@ -595,7 +595,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mixed / VL detail lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--e2e-slabs", default="1,1,2,2,2,2,2,2,1,1",
+    ap.add_argument("--e2e-slabs", default="1,2,3,4,3,2,1",
                     help="z-slabs of the end-to-end pipeline: a count (1: copy in, step, copy out in series) or "
                          "group layers per slab, e.g. 1,2,2,2,2,2,2,2,1")
     ap.add_argument("--e2e-sweep", default="",
