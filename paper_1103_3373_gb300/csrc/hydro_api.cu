@@ -37,7 +37,6 @@ struct State {
   int nsm[MAX_DEV] = {0};
   int smem_optin[MAX_DEV] = {0};
   bool attr_set[MAX_DEV][NKEY][2] = {{{false}}};  // [.][.][RUNS variant]
-  int occ[MAX_DEV][NKEY][3] = {{{0}}};  // cached occupancy per block size class
 };
 
 State& state() {
