@@ -127,6 +127,31 @@ def test_levels_runs_equal_groups_alone(small_levels, prec, scheme, recon, rs):
     for a, b in zip(ref, got):
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+    # run values are clamped to [1, groups left in the entry]: zeros and
+    # negatives mean every group alone, and a run that reaches the end of its
+    # level may overstate its length
+    for fill in ("nonpositive", "overstated"):
+        odd = []
+        for lv in small_levels:
+            z = lv["zrun"].copy()
+            if fill == "nonpositive":
+                z[:] = np.where(np.arange(len(z)) % 2 == 0, 0, -3)
+                want_alone = True
+            else:
+                tail = len(z) - 1
+                while tail > 0 and z[tail - 1] == z[tail] + 1:
+                    tail -= 1
+                z[tail:] += 1000
+                want_alone = False
+            odd.append(dict(lv, zrun=z))
+        lbo = batch(odd)
+        lbo.p.grid_ctas = 7
+        lbo._alloc_ws()
+        lbo.step()
+        got = snap(lbo)
+        for a, b in zip(ref, got):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y), (fill, want_alone)
 
 
 def test_autotune_picks_a_working_shape(small_levels):
