@@ -128,7 +128,7 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_OUTFLOW = 1 };                /* box edge
  *                to `chain` such groups without restarting, reading the
  *                planes between them from the interiors.  Values are
  *                clamped to [1, groups left in the entry]; NULL = every
- *                group alone.  Used by the CTU kernels (the other schemes
+ *                group alone.  Used by the unsplit schemes (the split ones
  *                advance every group alone): a launch with runs runs a
  *                variant of the kernel, whose results equal byte for byte
  *                those of the same launch with runs of one (every group

@@ -45,13 +45,13 @@ def _key(p: H.Params, tag):
 def chain_candidates(p: H.Params, tag):
     """Chain lengths worth timing: uniform fields of the unsplit schemes
     (0 = whole columns, up to CHAIN_MAX), and prepared groups given with
-    runs of z-continuations (tag "levels_runs", the CTU kernels; 0 = whole
-    runs, 1 = every group alone).  Other work does not chain."""
+    runs of z-continuations (tag "levels_runs"; 0 = whole runs, 1 = every
+    group alone).  Other work does not chain."""
     if p.scheme > H.CTU:
         return [p.chain]
     if tag == "uniform":
         return [0, 8, 4, 2]
-    if tag == "levels_runs" and p.scheme == H.CTU:
+    if tag == "levels_runs":
         return [0, 4, 2, 1]
     return [p.chain]
 

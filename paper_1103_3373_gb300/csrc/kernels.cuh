@@ -34,7 +34,7 @@ template <int PR, int RS, int SCH = 0> struct MaxThreads {
 };
 
 // RUNS: the variant that also streams runs of gathered groups as chains
-// (hydro_params.zrun; CTU only).  It is a kernel of its own so that the code
+// (hydro_params.zrun; the unsplit schemes).  It is a kernel of its own so that the code
 // of the other forms stays as it is; every form of one launch runs the same
 // compiled copy, so they give the same bytes.
 template <int SCH, int REC, int RS, int PR, int N, bool CH, bool RUNS = false>
@@ -130,7 +130,7 @@ template <int SCH, int REC, int RS, int PR, int N, bool CH> inline void put_kern
   using Tr = KTraits<SCH, REC, PR, N>;
   KernelEntry& e = tab[kernel_key(SCH, REC, CH ? 1 : 0, RS, PR)];
   e.fn = (const void*)&advance_kernel<SCH, REC, RS, PR, N, CH>;
-  if constexpr (SCH == CTU) e.fn_runs = (const void*)&advance_kernel<SCH, REC, RS, PR, N, CH, true>;
+  if constexpr (SCH <= CTU) e.fn_runs = (const void*)&advance_kernel<SCH, REC, RS, PR, N, CH, true>;
   e.ring_elems = Tr::RING;
   e.elem_bytes = (int)sizeof(typename Tr::T);
   e.max_threads = MaxThreads<PR, RS, SCH>::value;

@@ -315,7 +315,7 @@ def amr_hierarchy(n0=48, radii=(0.2,), center=(0.5, 0.5, 0.5), seed=7, mach=1.0,
     coarse and fine data are independent samples (not averages) of one field.
     Group order, every level: column by column (y, then x, then z fastest),
     so that the z-neighbours of a column are consecutive (the runs of
-    z-continuations that the CTU kernels stream as chains)."""
+    z-continuations that the unsplit kernels stream as chains)."""
     levels = []
     origin = column_origins(n0, n0, n0, N)
     nref = len(counts) if counts is not None else len(radii)

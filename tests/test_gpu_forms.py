@@ -70,11 +70,11 @@ def test_levels_batched_graph_and_oracle(small_levels):
 
 @pytest.mark.parametrize("prec", [H.FP64, H.FP32, H.FP32_MIXED])
 @pytest.mark.parametrize("scheme,recon,rs", [(H.CTU, H.PPM, H.RS_ROE), (H.CTU, H.PLM, H.RS_HLLC),
-                                             (H.VL, H.PLM, H.RS_HLLC)])
+                                             (H.VL, H.PLM, H.RS_HLLC), (H.MHM, H.PPM, H.RS_HLLE)])
 def test_levels_runs_equal_groups_alone(small_levels, prec, scheme, recon, rs):
     """Prepared groups given with runs of z-continuations (zrun: a level's
     columns, a refined group's z-pairs) stream through each run as one chain
-    in the CTU kernels (VL ignores the runs).  State, boundary fluxes and
+    in the unsplit schemes' kernels.  State, boundary fluxes and
     status equal, byte for byte, those of every group advanced alone (runs
     of one: the same kernel, which launches with runs use), for every chain
     limit and grid (grids of 7 and 3 CTAs give each CTA several groups, so
