@@ -581,6 +581,10 @@ def reference_arm(args, rank, world):
     return 0
 
 
+# slab partitions (group layers) the e2e leg chooses from on each box
+E2E_PARTITIONS = ("1,2,3,4,3,2,1", "1,1,2,2,2,2,2,2,1,1", "1,1,2,3,4,3,1,1", "2,4,4,4,2")
+
+
 def slab_arg(s):
     """'8' -> 8 equal slabs; '1,2,2,1' -> group layers per slab."""
     parts = [int(x) for x in str(s).split(",") if x.strip()]
@@ -595,9 +599,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mixed / VL detail lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--e2e-slabs", default="1,2,3,4,3,2,1",
-                    help="z-slabs of the end-to-end pipeline: a count (1: copy in, step, copy out in series) or "
-                         "group layers per slab, e.g. 1,2,2,2,2,2,2,2,1")
+    ap.add_argument("--e2e-slabs", default="auto",
+                    help="z-slabs of the end-to-end pipeline: auto (the fastest of E2E_PARTITIONS on this box), "
+                         "a count (1: copy in, step, copy out in series) or group layers per slab, e.g. 1,2,3,4,3,2,1")
     ap.add_argument("--e2e-sweep", default="",
                     help="also time the end-to-end step at these ';'-separated slab settings (e.g. '1;4;8;1,2,2,1')")
     ap.add_argument("--quick", action="store_true", help="main line only (no extra, cpu_baseline or e2e legs)")
@@ -725,7 +729,29 @@ def main():
                    "layers": hs.layers}
             del hs
             return out
-        e2e = e2e_run(slab_arg(args.e2e_slabs))
+        if args.e2e_slabs == "auto":
+            # the slab partition that suits this machine's host link: a few
+            # candidates timed over a few steps each, the fastest kept
+            trials = []
+            for S in E2E_PARTITIONS:
+                hs = RT.HostBoxStepper(U, make_params(H, H.FP32, dx), cfl=CFL, device=dev, slabs=slab_arg(S))
+                for _ in range(2):
+                    hs.step()
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(5):
+                    hs.step()
+                b.record()
+                torch.cuda.synchronize()
+                trials.append((a.elapsed_time(b) / 5, S))
+                del hs
+            best = min(trials)[1]
+            e2e = e2e_run(slab_arg(best))
+            e2e["partition_trials_ms"] = {S: round(t, 3) for t, S in trials}
+        else:
+            e2e = e2e_run(slab_arg(args.e2e_slabs))
         if e2e["slabs"] > 1:
             s = e2e_run(1)
             e2e["serial"] = {"value": s["value"], "ms_per_step": s["ms_per_step"]}
