@@ -716,17 +716,21 @@ def main():
             for _ in range(3):
                 hs.step()
             torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(ke):
+            # events on the stream the steps are issued on (each step's last
+            # operation makes it wait for the pipeline's streams)
+            st = hs.box.stream
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(ke + 1)]
+            evs[0].record(st)
+            for k in range(ke):
                 hs.step()
-            b.record()
+                evs[k + 1].record(st)
             torch.cuda.synchronize()
-            e_ms = a.elapsed_time(b)
+            e_ms = evs[0].elapsed_time(evs[ke])
+            per = [evs[k].elapsed_time(evs[k + 1]) for k in range(ke)]
             out = {"value": world * cells * ke / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": hs.h2d_bytes,
-                   "d2h_bytes_per_step": hs.d2h_bytes, "steps": ke, "ms_per_step": e_ms / ke, "slabs": hs.slabs,
-                   "layers": hs.layers}
+                   "d2h_bytes_per_step": hs.d2h_bytes, "steps": ke, "ms_per_step": e_ms / ke,
+                   "p50_step_ms": RT.percentile(per, 50), "p99_step_ms": RT.percentile(per, 99),
+                   "slabs": hs.slabs, "layers": hs.layers}
             del hs
             return out
         if args.e2e_slabs == "auto":
@@ -740,10 +744,10 @@ def main():
                 torch.cuda.synchronize()
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
-                a.record()
+                a.record(hs.box.stream)
                 for _ in range(5):
                     hs.step()
-                b.record()
+                b.record(hs.box.stream)
                 torch.cuda.synchronize()
                 trials.append((a.elapsed_time(b) / 5, S))
                 del hs
