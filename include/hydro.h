@@ -197,8 +197,8 @@ int hydro_gather_uniform(const void* field, int X, int Y, int Z, int bc, const i
                          int precision, void* U_out, void* stream);
 
 /*
- * hydro_advance_uniform — gather fused into the step for a uniform box tiled
- * by N^3 groups (group index (gz*GY + gy)*GX + gx): every CTA reads its
+ * hydro_advance_uniform — the preparation step's gather (Sec. 4.2) fused into
+ * the step of Sec. 2 for a uniform box tiled by N^3 groups (group index (gz*GY + gy)*GX + gx): every CTA reads its
  * groups' halos straight from field_in with the boundary condition bc and
  * writes their interiors to field_out (double buffering; no aliasing).  Each
  * CTA takes a contiguous run of groups in column order (z fastest) and
@@ -248,8 +248,9 @@ typedef struct hydro_level {
 #define HYDRO_CHAIN_MAX 32
 
 /*
- * hydro_advance_levels — one persistent launch that advances uneven per-AMR-
- * level group lists (or independent boxes) in one go: the work of all
+ * hydro_advance_levels — one persistent launch (Sec. 3.1: patch groups to
+ * thread blocks; Sec. 4.3: every level with its own time step) that advances
+ * uneven per-AMR-level group lists (or independent boxes) in one go: the work of all
  * entries is one flat list of groups shared round-robin by the CTAs.  Every
  * entry has its own dx and dt; scheme, reconstruction, limiter, solver,
  * precision and ghost width come from p (p->dt and p->dx are ignored).
@@ -275,7 +276,8 @@ int hydro_cfl_dt(const void* U, int G, long long group_stride, long long var_str
                  double* smax_dev, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * hydro_conserved_totals — global sums of the five conserved variables over
+ * hydro_conserved_totals — global sums of the five conserved variables (the
+ * quantities that the conservative update of Sec. 2 step (4) keeps) over
  * the same addressing as hydro_cfl_dt, accumulated in FP64 (the
  * conservation check of the mixed-precision form).
  *   totals_dev  device double[5].
@@ -318,8 +320,8 @@ int hydro_cfl_dt_boxes(const hydro_cfl_box* boxes, int nbox, int precision, doub
                        void* stream);
 
 /*
- * hydro_cfl_dt_noalloc — hydro_cfl_dt for callers that cannot allocate device
- * memory.  The paper has no counterpart: it serves code that runs where no
+ * hydro_cfl_dt_noalloc — hydro_cfl_dt (the time step of Sec. 4.3) for callers
+ * that cannot allocate device memory.  The paper has no counterpart: it serves code that runs where no
  * allocator is reachable, e.g. a plug-in enqueued inside another framework's
  * CUDA graph capture (where cudaMalloc is not allowed) or a host runtime
  * that hands out only the input and output buffers.  It allocates nothing

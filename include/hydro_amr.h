@@ -81,8 +81,9 @@ typedef struct hydro_amr_level {
 } hydro_amr_level;
 
 /*
- * hydro_amr_map — fill map (int[Z/N][Y/N][X/N]) with -1, then store each
- * group's index at its slot origin/N.  Origins must be multiples of N inside
+ * hydro_amr_map — the level lookup that the preparation step (Sec. 4.2) and
+ * the corrections (Sec. 4.3) use: fill map (int[Z/N][Y/N][X/N]) with -1,
+ * then store each group's index at its slot origin/N.  Origins must be multiples of N inside
  * the box (else HYDRO_EINVAL is not detectable on the host: such groups set
  * HYDRO_AMR_ENESTING and are skipped); a slot claimed twice sets
  * HYDRO_AMR_EDUPLICATE.
@@ -119,7 +120,8 @@ int hydro_amr_reflux(const hydro_amr_level* coarse, const void* coarse_flux, con
                      int precision, unsigned* dev_error, void* stream);
 
 /*
- * hydro_amr_restrict — every coarse cell of coarse->U covered by a group of
+ * hydro_amr_restrict — the correction of the coarse-grid data (Sec. 4.3): every
+ * coarse cell of coarse->U covered by a group of
  * `fine` (fine->U after its last substep) takes the mean of its 8 fine
  * cells (in place).
  */

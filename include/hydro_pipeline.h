@@ -40,7 +40,8 @@ extern "C" {
 typedef struct hydro_pipeline hydro_pipeline;
 
 /*
- * hydro_pipeline_create — plan the slabs of an X x Y x Z box (multiples of N)
+ * hydro_pipeline_create — the asynchronous-copy scheme of Sec. 4.1: plan the
+ * slabs of an X x Y x Z box (multiples of N)
  * for schemes needing at most `ghost` halo cells (hydro_required_ghost).
  *   nslab >= 1 slabs; layers = NULL splits the Z/N group layers evenly, else
  *   layers[s] >= 1 group layers of slab s (sum Z/N).
@@ -53,7 +54,8 @@ int hydro_pipeline_create(int X, int Y, int Z, int N, int ghost, int bc, int nsl
                           hydro_pipeline** out);
 
 /*
- * hydro_pipeline_step — one step; its completion (state and dt on the host)
+ * hydro_pipeline_step — one step with its copies overlapped (Sec. 4.1); its
+ * completion (state and dt on the host)
  * is ordered before later work on `stream`.  No host synchronisation.
  *   Chained steps: when host_in is the last step's host_out, dev_in is
  *   neither of the last step's device buffers and dev_out is not the last
@@ -86,11 +88,11 @@ int hydro_pipeline_step(hydro_pipeline* h, const hydro_params* p, const void* ho
                         void* red_ws, size_t red_ws_bytes, void* ws2, size_t ws2_bytes, void* stream);
 
 /* hydro_pipeline_workspace_bytes — device scratch hydro_pipeline_step needs
- * as red_ws (the CFL reduction's); 0 for NULL. */
+ * as red_ws (the CFL reduction's, Sec. 4.3); 0 for NULL. */
 size_t hydro_pipeline_workspace_bytes(const hydro_pipeline* h);
 
 /*
- * hydro_pipeline_plan — the copy plan hydro_pipeline_create makes, on the
+ * hydro_pipeline_plan — the copy plan (Sec. 4.1) hydro_pipeline_create makes, on the
  * host only (no device call): zb[nslab+1] slab boundaries (planes) and, per
  * slab, up to two input plane ranges chunks[s] = {lo0, hi0, lo1, hi1} (an
  * empty range has lo = hi) whose copy completes slab s's input and halo, in
@@ -99,8 +101,8 @@ size_t hydro_pipeline_workspace_bytes(const hydro_pipeline* h);
  */
 int hydro_pipeline_plan(int Z, int N, int ghost, int bc, int nslab, const int* layers, int* zb, int* chunks);
 
-/* hydro_pipeline_destroy — release streams, events and the object (NULL: no-op).
- * Synchronises the pipeline's own streams first. */
+/* hydro_pipeline_destroy — release the streams and events of the Sec. 4.1 scheme
+ * and the object (NULL: no-op).  Synchronises the pipeline's own streams first. */
 int hydro_pipeline_destroy(hydro_pipeline* h);
 
 #ifdef __cplusplus

@@ -2,6 +2,7 @@
 loads, and exports every entry point the headers in include/ declare.  No compute
 call is made (there is no GPU in the CPU suite)."""
 import ctypes
+import glob
 import os
 import re
 import shutil
@@ -123,3 +124,28 @@ def test_python_constants_match_the_header():
         assert macro["HYDRO_" + name] == getattr(H, name), name
     for name in ("ST_ROE_FALLBACK", "ST_NEG_DENS", "ST_NEG_PRES", "ST_NAN", "ST_EXACT_FAIL"):
         assert macro["HYDRO_" + name] == getattr(H, name), name
+
+
+# query and error calls, and the measurement kernel: no passage of the paper
+# defines them
+NO_PASSAGE = {"hydro_required_ghost", "hydro_workspace_bytes", "hydro_max_block_threads", "hydro_strerror",
+              "hydro_last_cuda_error", "hydro_cfl_workspace_bytes", "hydro_cfl_boxes_workspace_bytes",
+              "hydro_fma_peak"}
+
+
+def test_every_call_cites_its_passage():
+    """Each declaration of the C ABI has one comment block headed by its name
+    that cites the section of the paper defining the operation (query, error
+    and measurement calls excepted)."""
+    missing = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = open(path).read()
+        blocks = re.findall(r"/\*.*?\*/", src, re.S)
+        for name in re.findall(r"^(?:int|size_t|const char\*|double|void)\s+(hydro_\w+)\s*\(", src, re.M):
+            if name in NO_PASSAGE:
+                continue
+            # the block whose heading is "name — ..."
+            heads = [b for b in blocks if re.search(r"(?:^/\*|\n \*)\s*%s\b[^\n]*\u2014" % name, b)]
+            if len(heads) != 1 or "Sec." not in heads[0]:
+                missing.append(name)
+    assert not missing, missing
