@@ -390,6 +390,73 @@ def cpu_baseline(U, dx, budget_s=12.0):
             "single_core": {"value": S1 * 4096 / el1, "groups": S1, "seconds": el1}}
 
 
+def oracle_configs(H, RT, W, torch, dev, cpu_c2=None, gpu_c2=None):
+    """The oracle (one core and all host cores) beside the GPU on the other
+    stated workloads, and the paper's "speed-up over one CPU core" as GPU /
+    oracle-1-core (a different CPU and a different code than the paper's):
+      c1      32^3 Sod along x, FP64, MHM + PLM minmod + Roe, outflow, CFL 0.5,
+              10 steps (GPU: FP64);
+      c4_cut  the central 64^3 cells of the 512^3 Sedov start, one
+              CTU + PPM + HLLC step, outflow (GPU: FP64 and the FP32 mixed form);
+      c2      the headline box (from the main line and the cpu_baseline leg)."""
+    import oracle as O
+    out = {}
+    N = 16
+
+    def gpu_rate(U, p, bc, steps, cfl):
+        box = RT.UniformBox(U, p, cfl=cfl, bc=bc, device=dev)
+        box.compute_dt()
+        for _ in range(2):
+            box.step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(box.stream)
+        for _ in range(steps):
+            box.step()
+        b.record(box.stream)
+        torch.cuda.synchronize()
+        cells = U[0].size
+        return cells * steps / (a.elapsed_time(b) / 1e3)
+
+    def oracle_rate(U, P, ghost, bc, steps, cfl, nthreads=None):
+        n = U.shape[1]
+        orig = W.group_origins(n, n, n, N)
+        dx = P.dx
+        t = time.perf_counter()
+        for _ in range(steps):
+            P.dt = O.cfl_dt(U, dx, cfl, P.gamma, P.dens_floor, P.pres_floor)
+            kw = {} if nthreads is None else {"nthreads": nthreads}
+            U = W.scatter_groups(O.advance(P, O.gather(U, orig, N, ghost, bc=bc), N, **kw)[0], n, n, n)
+        return U[0].size * steps / (time.perf_counter() - t)
+
+    # C1
+    U = W.sod(32, 0)
+    dx = (1.0 / 32,) * 3
+    P = O.Params(scheme=O.MHM, recon=O.PLM, riemann=O.ROE, limiter=O.MINMOD, dx=dx)
+    p = H.Params(scheme=H.MHM, recon=H.PLM, riemann=H.RS_ROE, limiter=H.LIM_MINMOD, precision=H.FP64, dx=dx)
+    c1 = {"oracle_all_cores": oracle_rate(U, P, 2, 1, 10, 0.5), "oracle_1_core": oracle_rate(U, P, 2, 1, 10, 0.5, 1),
+          "gpu_fp64": gpu_rate(U, p, H.BC_OUTFLOW, 10, 0.5)}
+    c1["gpu_fp64_over_1_core"] = c1["gpu_fp64"] / c1["oracle_1_core"]
+    out["c1"] = c1
+    # C4 cut
+    U = W.sedov(512, gamma=SEDOV_GAMMA, window=64)
+    dx = (1.0 / 512,) * 3
+    P = O.Params(scheme=O.CTU, recon=O.PPM, riemann=O.HLLC, limiter=O.MINMOD, gamma=SEDOV_GAMMA, dx=dx,
+                 **SEDOV_FLOORS)
+    c4 = {"oracle_all_cores": oracle_rate(U, P, 3, 1, 1, 0.4), "oracle_1_core": oracle_rate(U, P, 3, 1, 1, 0.4, 1),
+          "gpu_fp64": gpu_rate(U, _sedov_params(H, H.FP64, dx), H.BC_OUTFLOW, 10, 0.4),
+          "gpu_fp32_mixed": gpu_rate(U, _sedov_params(H, H.FP32_MIXED, dx), H.BC_OUTFLOW, 10, 0.4)}
+    c4["gpu_fp32_mixed_over_1_core"] = c4["gpu_fp32_mixed"] / c4["oracle_1_core"]
+    out["c4_cut"] = c4
+    if cpu_c2 and gpu_c2:
+        out["c2"] = {"oracle_all_cores": cpu_c2["value"], "oracle_1_core": cpu_c2["single_core"]["value"],
+                     "gpu_fp32": gpu_c2, "gpu_fp32_over_1_core": gpu_c2 / cpu_c2["single_core"]["value"]}
+    out["cores"] = O.max_threads()
+    out["unit"] = UNIT
+    return out
+
+
 SEDOV_GAMMA = 5.0 / 3.0
 SEDOV_FLOORS = dict(dens_floor=1e-12, pres_floor=1e-12)
 XI0 = 1.15
@@ -829,6 +896,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(U, dx)
+        if not args.no_extra:
+            extra["oracle_configs"] = oracle_configs(H, RT, W, torch, dev, cpu, value)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
