@@ -149,3 +149,18 @@ def test_every_call_cites_its_passage():
             if len(heads) != 1 or "Sec." not in heads[0]:
                 missing.append(name)
     assert not missing, missing
+
+
+def test_readme_c_example_compiles_against_the_header(tmp_path):
+    """The C example in README.md is valid C99 against include/hydro.h."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    import subprocess
+    src = open(os.path.join(ROOT, "README.md")).read()
+    code = re.search(r"```c\n(.*?)```", src, re.S).group(1)
+    f = tmp_path / "example.c"
+    f.write_text(code)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I" + os.path.join(ROOT, "include"),
+                        str(f)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
