@@ -279,3 +279,29 @@ def test_sedov_taylor_radius_and_spherical_symmetry():
             np.testing.assert_allclose(r, rays[0], rtol=0, atol=1e-12)
         R_num = (np.argmax(rays[0]) + 0.5) / n
         assert abs(R_num - xi0 * t ** 0.4) <= 1.0 / n, (R, R_num)
+
+
+def test_stored_flop_counts_are_the_oracles():
+    """The roofline numerator bench.py reads (data/flops_per_cell.json) is what
+    oracle/count_ops.py computes now: the headline and VL entries recounted
+    on the same workload equal the stored values."""
+    import json
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    import importlib.util
+    # loaded under a name of its own: as the submodule oracle.count_ops it would
+    # shadow the package's count_ops function, which it calls
+    spec = importlib.util.spec_from_file_location("oracle_count_script", os.path.join(root, "oracle", "count_ops.py"))
+    C = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(C)
+    stored = json.load(open(os.path.join(root, "paper_1103_3373_gb300", "data", "flops_per_cell.json")))["entries"]
+    n, N = 32, 16
+    U = W.lognormal(n, seed=1, mach=1.5)
+    dx = (1.0 / n,) * 3
+    dt = O.cfl_dt(U, dx, 0.4)
+    for scheme, recon, rs, key in ((O.CTU, O.PPM, O.ROE, "ctu-ppm-roe"), (O.VL, O.PLM, O.HLLC, "vl-plm-hllc")):
+        g = O.required_ghost(scheme, recon)
+        Ug = O.gather(U, W.group_origins(n, n, n, N), N, g, bc=0)
+        groups = [(Ug[i], dt, dx) for i in range(0, Ug.shape[0], 3)]
+        got = C.count(scheme, recon, rs, groups)
+        assert got["flops"] == pytest.approx(stored[key]["flops"], rel=1e-12), key
