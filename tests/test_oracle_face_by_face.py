@@ -227,31 +227,43 @@ CASES = [
     (O.MHM, O.PLM, O.HLLE, O.HYBRID),
     (O.VL, O.PLM, O.HLLC, O.MINMOD),
     (O.VL, O.PPM, O.ROE, O.VANLEER),
+    # characteristic-variable reconstruction (Sec. 2)
+    (O.CTU, O.PPM, O.ROE, O.MINMOD, 1),
+    (O.MHM, O.PLM, O.HLLC, O.VANALBADA, 1),
+    (O.VL, O.PLM, O.ROE, O.VANLEER, 1),
 ]
 
 
-def setup(scheme, recon, solver, lim, N=2, seed=11):
+def setup(scheme, recon, solver, lim, characteristic=0, N=2, seed=11):
     g = O.required_ghost(scheme, recon)
     Upad = tiny_group(N, g, seed)
     dx = (1.0, 0.7, 1.3)
     dt = O.cfl_dt(Upad[None], dx, 0.3, GAMMA)
     P = O.Params(scheme=scheme, recon=recon, riemann=solver, limiter=lim, fallback=O.HLLE, dt=dt, dx=dx,
-                 gamma=GAMMA)
+                 gamma=GAMMA, characteristic=characteristic)
     Uo, flux, st = O.advance(P, Upad[None], N=N, ghost=g)
     assert int(st[0]) & ~ROE_FALLBACK == 0
     return P, Upad, g, Uo[0], flux[0]
 
 
-@pytest.mark.parametrize("scheme,recon,solver,lim", CASES)
-def test_cell_composed_face_by_face(scheme, recon, solver, lim):
+def case_id(case):
+    names = ({O.CTU: "ctu", O.MHM: "mhm", O.VL: "vl"}, {O.PLM: "plm", O.PPM: "ppm"},
+             {O.EXACT: "exact", O.HLLE: "hlle", O.HLLC: "hllc", O.ROE: "roe"},
+             {O.MINMOD: "minmod", O.VANLEER: "vanleer", O.VANALBADA: "vanalbada", O.HYBRID: "hybrid"})
+    parts = [n[v] for n, v in zip(names, case)]
+    return "-".join(parts + (["char"] if len(case) > 4 and case[4] else []))
+
+
+@pytest.mark.parametrize("case", CASES, ids=case_id)
+def test_cell_composed_face_by_face(case):
     """N = 2 with the scheme's ghost width: every boundary-face flux the
     group step stores, and every updated cell, equal the face-by-face
     composition bit for bit (the oracle is built without floating-point
     contraction, and the numpy arithmetic here takes its operations in the
     same order)."""
     N = 2
-    P, Upad, g, Uo, flux = setup(scheme, recon, solver, lim, N)
-    C = COMPOSERS[scheme](P, Upad, N, g)
+    P, Upad, g, Uo, flux = setup(*case, N=N)
+    C = COMPOSERS[case[0]](P, Upad, N, g)
     # stored fluxes: flux[2d + side, v, a, b] on the face -1/2 (side 0) or
     # N-1/2 (side 1) along d; (a, b) = (z, y) for x, (z, x) for y, (y, x) for z
     for d in range(3):
@@ -280,7 +292,7 @@ def test_composition_detects_planted_mistakes(scheme, plant):
     composition moves the cell's update far beyond rounding."""
     case = next(c for c in CASES if c[0] == scheme)
     N = 2
-    P, Upad, g, Uo, _ = setup(*case, N)
+    P, Upad, g, Uo, _ = setup(*case, N=N)
     bad = COMPOSERS[scheme](P, Upad, N, g, plant=plant).update((0, 1, 1))
     err = np.abs(bad - Uo[:, 1, 1, 0]).max() / np.abs(Uo).max()
     assert err > 1e-6
