@@ -216,13 +216,14 @@ def time_box(box, steps, warmup, torch, sampler=None):
     return step_ms, float(np.mean(adv_ms)), t0.elapsed_time(t1), clocks
 
 
-def amr_leg(H, RT, W, torch, dev, steps=20):
+def amr_leg(H, RT, W, torch, dev, steps=20, block_threads=0):
     """AMR-shaped batch: 4 levels of 4096/2500/1500/800 halo-prepared groups
     (refined where |grad rho|/rho > 0.3 on a seeded 128^3 lognormal root), per-
     level dx and device dt.  FP32 batched persistent launch replayed from a
-    CUDA graph and autotuned, against the same FP32 step as one launch per
-    level, the same batched launch with every group advanced alone, and the
-    plain FP64 per-level launch (groups alone)."""
+    CUDA graph and autotuned (block_threads > 0: that fixed shape with whole
+    runs as chains, no tuning launches, for profiling), against the same FP32
+    step as one launch per level, the same batched launch with every group
+    advanced alone, and the plain FP64 per-level launch (groups alone)."""
     t = time.perf_counter()
     levels = W.amr_levels()
     gen_s = time.perf_counter() - t
@@ -230,7 +231,13 @@ def amr_leg(H, RT, W, torch, dev, steps=20):
            "flagged_fraction": [l["flagged_fraction"] for l in levels]}
     p = make_params(H, H.FP32, (1.0, 1.0, 1.0))
     lb = RT.LevelBatch(levels, p, cfl=CFL, device=dev)
-    tb = lb.tune()
+    if block_threads:
+        lb.p.block_threads = min(block_threads, H.hydro_max_block_threads(lb.p))
+        lb.p.chain = 0
+        lb._alloc_ws()
+        tb = {"block_threads": lb.p.block_threads, "chain": 0}
+    else:
+        tb = lb.tune()
     lb.capture()
     cells = lb.cells
     for _ in range(3):
@@ -886,7 +893,7 @@ def main():
             del bx
         torch.cuda.empty_cache()
         if "amr_levels" in legs:
-            extra["amr_levels"] = amr_leg(H, RT, W, torch, dev)
+            extra["amr_levels"] = amr_leg(H, RT, W, torch, dev, block_threads=args.block_threads)
         if "amr_hierarchy" in legs:
             extra["amr_hierarchy"] = amr_hierarchy_leg(H, RT, W, torch, dev)
         torch.cuda.empty_cache()
