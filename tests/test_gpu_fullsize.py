@@ -127,15 +127,16 @@ def test_c3_stated_sizes_sampled_levels(amr_levels_full):
         G = lv["U"].shape[0]
         dt = lb.dts[l].item()
         dx = (lv["dx"],) * 3
+        # the level's dt is its own CFL reduction over its prepared groups
+        # (FP32 per-cell speeds); the oracle takes its own
+        dt_o = O.cfl_dt(lv["U"], dx, 0.4, 1.4, 1e-6, 1e-6)
+        assert dt == pytest.approx(dt_o, rel=1e-6)
         pick = np.unique(np.concatenate([[0, G - 1], rng.choice(G, 4, replace=False)]))
         Ul = lv["U"][pick].astype(np.float64)
-        P = O.Params(scheme=O.CTU, recon=O.PPM, riemann=O.ROE, dt=dt, dx=dx, dens_floor=1e-6, pres_floor=1e-6)
+        P = O.Params(scheme=O.CTU, recon=O.PPM, riemann=O.ROE, dt=dt_o, dx=dx, dens_floor=1e-6, pres_floor=1e-6)
         ref, ref_flux, ref_st = O.advance(P, Ul, 16)
         idx = torch.as_tensor(pick, device=lb.U_out[l].device)
         assert_close(lb.U_out[l][idx].double().cpu().numpy(), ref, H.FP32, "level %d state" % l)
         assert_close(lb.flux[l][idx].double().cpu().numpy(), ref_flux, H.FP32, "level %d flux" % l, axis_var=2)
         st = lb.status[l].cpu().numpy().astype(np.uint32)
         assert np.array_equal(st[pick] & H.ST_ERROR_MASK, ref_st & H.ST_ERROR_MASK)
-        # the level's dt is its own CFL reduction over its prepared groups
-        # (FP32 per-cell speeds)
-        assert dt == pytest.approx(O.cfl_dt(lv["U"], dx, 0.4, 1.4, 1e-6, 1e-6), rel=1e-6)

@@ -90,8 +90,9 @@ def test_split_sod_ten_steps_fp64(scheme):
     org = W.group_origins(16, n, 16, N)
     g = O.required_ghost(scheme, 0)
     for k in range(10):
-        dt = box.dt.item()
-        assert dt == pytest.approx(O.cfl_dt(Uo, dx, 0.4), rel=1e-14)
+        # the oracle takes its own dt; the device's agrees
+        dt = O.cfl_dt(Uo, dx, 0.4)
+        assert box.dt.item() == pytest.approx(dt, rel=1e-14)
         P = O.Params(scheme=scheme, limiter=O.VANLEER, dt=dt, dx=dx, split_order=k % 2)
         Uo = W.scatter_groups(O.advance(P, O.gather(Uo, org, N, g, bc=1), N)[0], 16, n, 16)
         box.step()
