@@ -301,7 +301,9 @@ int hydro_conserved_totals(const void* U, int G, long long group_stride, long lo
  *   workspace   device scratch of hydro_cfl_boxes_workspace_bytes() bytes.
  * 1 <= nbox <= HYDRO_CFL_MAX_BOXES (call again for more).  Returns
  * HYDRO_OK, HYDRO_EINVAL (null pointer, nbox out of range, G or cells < 0,
- * dx or dt_scale not positive and finite, gamma <= 1, cfl <= 0),
+ * dx or dt_scale not positive and finite, gamma <= 1, cfl <= 0, ghost < 0,
+ * or ghost > 0 with interior_n < 1, cells != interior_n^3 or var_stride
+ * below M^3),
  * HYDRO_EWORKSPACE, or HYDRO_ECUDA.  Allocates nothing.
  */
 #define HYDRO_CFL_MAX_BOXES 256
@@ -313,6 +315,13 @@ typedef struct hydro_cfl_box {
   double* dt_dev;
   double* smax_dev;
   double dt_scale;
+  /* ghost > 0: each group is a halo-padded cube of M = interior_n + 2 ghost
+   * cells per edge (x fastest, at U + g*group_stride + v*var_stride), cells
+   * = interior_n^3, and only the interior cells are reduced: the time step
+   * of a level of halo-prepared groups, whose ghost cells belong to other
+   * groups or are interpolated from the coarser level.  var_stride must be
+   * at least M^3.  ghost = 0: the cells of a group are contiguous (above). */
+  int interior_n, ghost;
 } hydro_cfl_box;
 size_t hydro_cfl_boxes_workspace_bytes(void);
 int hydro_cfl_dt_boxes(const hydro_cfl_box* boxes, int nbox, int precision, double gamma, double dens_floor,

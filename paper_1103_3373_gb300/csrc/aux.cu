@@ -207,14 +207,16 @@ __global__ void cfl_final_kernel(const double* __restrict__ part, int nseg, int 
 // ---- CFL time step of many boxes in one pass (continuous batching, AMR
 // levels): the table of boxes is a kernel argument; box b owns the pass-1
 // CTAs [first_b, first_b + nblk_b), each reducing one contiguous chunk of the
-// box's G * cells cells exactly as cfl_partial_kernel does; pass 2 runs one
+// box's G * cells cells exactly as cfl_partial_kernel does (a box of
+// halo-padded groups numbers only their interior cells, x fastest, and maps
+// each to its place in the padded cube); pass 2 runs one
 // CTA per box; an optional pass 3 takes min_b scale_b dt_b.  A box's dt
 // equals hydro_cfl_dt's on the same data bit for bit: both are maxima of the
 // same per-cell FP64 values, divided and inverted the same way.
 struct CflBoxDev {
   const void* U;
   long long gstride, vstride, cells;
-  int G, first, nblk, pad;
+  int G, first, nblk, n, gh, pad;  // n, gh: interior edge and ghost width (gh = 0: contiguous cells)
   double dx[3];
   double* dt;
   double* smax;
@@ -251,7 +253,15 @@ __global__ void __launch_bounds__(256) cfl_boxes_partial_kernel(const __grid_con
   Gas<S> gas{(S)gamma, (S)(gamma - 1.0), (S)dfloor, (S)pfloor, (S)(1.0 / (gamma - 1.0))};
   for (long long e = begin + threadIdx.x; e < end; e += blockDim.x) {
     const long long gi = e / bx.cells, i = e - gi * bx.cells;
-    const S* b = U + gi * bx.gstride + i;
+    long long off = i;
+    if (bx.gh > 0) {
+      const int n = bx.n, M = n + 2 * bx.gh;
+      const int z = (int)(i / ((long long)n * n));
+      const int r = (int)(i - (long long)z * n * n);
+      const int y = r / n, x = r - y * n;
+      off = ((long long)(z + bx.gh) * M + (y + bx.gh)) * M + (x + bx.gh);
+    }
+    const S* b = U + gi * bx.gstride + off;
     S u[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = b[v * bx.vstride];
@@ -454,6 +464,8 @@ cudaError_t launch_cfl_boxes(const hydro_cfl_box* boxes, int n, int dbl, double 
     t.vstride = boxes[b].var_stride;
     t.cells = boxes[b].cells;
     t.G = boxes[b].G;
+    t.n = boxes[b].interior_n;
+    t.gh = boxes[b].ghost;
     t.pad = 0;
     for (int d = 0; d < 3; ++d) t.dx[d] = boxes[b].dx[d];
     t.dt = boxes[b].dt_dev;

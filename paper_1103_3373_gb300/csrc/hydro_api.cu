@@ -481,6 +481,12 @@ int hydro_cfl_dt_boxes(const hydro_cfl_box* boxes, int nbox, int precision, doub
     if (!x.U || !x.dt_dev || x.G < 0 || x.cells < 0 || !finite_pos(x.dt_scale)) return HYDRO_EINVAL;
     for (int d = 0; d < 3; ++d)
       if (!finite_pos(x.dx[d])) return HYDRO_EINVAL;
+    if (x.ghost < 0) return HYDRO_EINVAL;
+    if (x.ghost > 0) {
+      const long long n = x.interior_n, M = n + 2LL * x.ghost;
+      if (n < 1 || n > 1024 || x.ghost > 1024 || x.cells != n * n * n || x.var_stride < M * M * M)
+        return HYDRO_EINVAL;
+    }
   }
   if (!workspace || workspace_bytes < cfl_boxes_workspace_bytes()) return HYDRO_EWORKSPACE;
   int dev;

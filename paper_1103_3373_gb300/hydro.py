@@ -110,7 +110,8 @@ class Params:
 class _CCflBox(ctypes.Structure):
     _fields_ = [("U", ctypes.c_void_p), ("G", ctypes.c_int), ("group_stride", ctypes.c_longlong),
                 ("var_stride", ctypes.c_longlong), ("cells", ctypes.c_longlong), ("dx", ctypes.c_double * 3),
-                ("dt_dev", ctypes.c_void_p), ("smax_dev", ctypes.c_void_p), ("dt_scale", ctypes.c_double)]
+                ("dt_dev", ctypes.c_void_p), ("smax_dev", ctypes.c_void_p), ("dt_scale", ctypes.c_double),
+                ("interior_n", ctypes.c_int), ("ghost", ctypes.c_int)]
 
 
 CFL_MAX_BOXES = 256
@@ -426,18 +427,26 @@ def hydro_cfl_boxes_workspace_bytes():
 
 def make_cfl_boxes(boxes, precision):
     """ctypes table for hydro_cfl_dt_boxes from (U, dx, dt_out[, dt_scale[,
-    smax_out]]) tuples: U a contiguous field [5,Z,Y,X] or groups
-    [G,5,...]; dt_out / smax_out 1-element float64 device tensors."""
+    smax_out[, ghost]]]) tuples: U a contiguous field [5,Z,Y,X] or groups
+    [G,5,...]; dt_out / smax_out 1-element float64 device tensors; ghost > 0:
+    U holds halo-padded groups [G,5,M,M,M] and only their (M - 2 ghost)^3
+    interior cells count."""
     dt = _storage_dtype(precision)
     arr = (_CCflBox * len(boxes))()
     for k, b in enumerate(boxes):
         U, dx, dt_out = b[0], b[1], b[2]
         scale = float(b[3]) if len(b) > 3 else 1.0
         smax = b[4] if len(b) > 4 else None
+        ghost = int(b[5]) if len(b) > 5 else 0
         G, gs, vs, cells = _red_layout(U)
         e = arr[k]
         e.U = _ptr(U, "U", dt)
         e.G, e.group_stride, e.var_stride, e.cells = G, gs, vs, cells
+        if ghost > 0:
+            if U.dim() != 5 or U.shape[1] != 5 or not (U.shape[2] == U.shape[3] == U.shape[4]):
+                raise ValueError("ghost > 0 needs halo-padded groups [G,5,M,M,M]")
+            n = U.shape[-1] - 2 * ghost
+            e.interior_n, e.ghost, e.cells = n, ghost, n ** 3
         for d_ in range(3):
             e.dx[d_] = float(dx[d_])
         e.dt_dev = _ptr(dt_out, "dt_out", "float64")

@@ -180,7 +180,8 @@ def percentile(xs, q):
 class LevelBatch:
     """Uneven per-AMR-level lists of halo-prepared groups advanced by ONE
     persistent launch (hydro_advance_levels), each level with its own dx and
-    its own device dt from its own CFL reduction (Sec. 4.3 per level).
+    its own device dt from its own CFL reduction over the interior cells of
+    its groups (Sec. 4.3 per level).
 
     step() = one CFL reduction per level + the batched launch; it takes no
     host synchronisation and can be captured once into a CUDA graph
@@ -216,8 +217,10 @@ class LevelBatch:
         # autotuner cache tag: chain lengths are candidates only with runs
         self.tune_tag = "levels_runs" if any(z is not None for z in self.zrun) else "levels"
         self.red_ws = torch.empty(H.hydro_cfl_boxes_workspace_bytes(), dtype=torch.uint8, device=self.dev)
-        self.cfl_boxes = H.make_cfl_boxes([(self.U_in[l], self.dx[l], self.dts[l]) for l in range(len(self.U_in))],
-                                          params.precision)
+        # each level's dt from its groups' interior cells (the ghosts belong
+        # to other groups or are interpolated from the coarser level)
+        self.cfl_boxes = H.make_cfl_boxes([(self.U_in[l], self.dx[l], self.dts[l], 1.0, None, ghost)
+                                           for l in range(len(self.U_in))], params.precision)
         self.stream = stream
         self._alloc_ws()
         self.graph = None

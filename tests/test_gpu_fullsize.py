@@ -127,9 +127,9 @@ def test_c3_stated_sizes_sampled_levels(amr_levels_full):
         G = lv["U"].shape[0]
         dt = lb.dts[l].item()
         dx = (lv["dx"],) * 3
-        # the level's dt is its own CFL reduction over its prepared groups
-        # (FP32 per-cell speeds); the oracle takes its own
-        dt_o = O.cfl_dt(lv["U"], dx, 0.4, 1.4, 1e-6, 1e-6)
+        # the level's dt is its own CFL reduction over its groups' interior
+        # cells (FP32 per-cell speeds); the oracle takes its own
+        dt_o = O.cfl_dt(lv["U"][:, :, 3:-3, 3:-3, 3:-3], dx, 0.4, 1.4, 1e-6, 1e-6)
         assert dt == pytest.approx(dt_o, rel=1e-6)
         pick = np.unique(np.concatenate([[0, G - 1], rng.choice(G, 4, replace=False)]))
         Ul = lv["U"][pick].astype(np.float64)

@@ -369,3 +369,44 @@ def test_cfl_dt_boxes_equals_per_box(torch_dev, prec):
     with pytest.raises(H.HydroError) as e:
         H.hydro_cfl_dt_boxes(boxes[:1], 0.45, ws1[:64], precision=prec)
     assert e.value.code == H.EWORKSPACE
+
+
+@pytest.mark.parametrize("prec", [H.FP64, H.FP32])
+def test_cfl_dt_boxes_interior_of_padded_groups(torch_dev, prec):
+    """A box of halo-padded groups with ghost > 0 reduces only the groups'
+    interior cells: its dt and max speed equal hydro_cfl_dt's on the copied-out
+    interiors bit for bit, and the oracle's dt over the same cells; a NaN in a
+    ghost cell is not seen, one in an interior cell is.  Malformed interior
+    descriptions are refused."""
+    torch, dev = torch_dev
+    dtp = tdtype(prec)
+    g = 3
+    grouped = torch.tensor(lognormal_groups(n=32, g=g, seed=8, prec=prec)[1], dtype=dtp, device=dev)
+    inner = grouped[:, :, g:-g, g:-g, g:-g].contiguous()
+    dx = (1 / 32, 1 / 30, 1 / 34)
+    ws1 = torch.empty(H.hydro_cfl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    ref = torch.zeros(2, dtype=torch.float64, device=dev)
+    H.hydro_cfl_dt(inner, dx, 0.45, ref[0:1], ws1, precision=prec, smax_out=ref[1:2])
+    ws = torch.empty(H.hydro_cfl_boxes_workspace_bytes(), dtype=torch.uint8, device=dev)
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+    boxes = [(grouped, dx, out[0:1], 1.0, out[1:2], g)]
+    H.hydro_cfl_dt_boxes(boxes, 0.45, ws, precision=prec)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+    dt_o = O.cfl_dt(inner.double().cpu().numpy(), dx, 0.45)
+    assert out[0].item() == (dt_o if prec == H.FP64 else pytest.approx(dt_o, rel=1e-6))
+    # a ghost cell is not part of the reduction; an interior cell is
+    grouped[1, 0, 0, 0, 0] = float("nan")
+    H.hydro_cfl_dt_boxes(boxes, 0.45, ws, precision=prec)
+    torch.cuda.synchronize()
+    assert out[0].item() == ref[0].item()
+    grouped[1, 0, g + 2, g + 5, g + 7] = float("nan")
+    H.hydro_cfl_dt_boxes(boxes, 0.45, ws, precision=prec)
+    torch.cuda.synchronize()
+    assert np.isnan(out[0].item())
+    for field, value in (("ghost", -1), ("cells", 5), ("interior_n", 0), ("var_stride", 10)):
+        arr = H.make_cfl_boxes(boxes, prec)
+        setattr(arr[0], field, value)
+        with pytest.raises(H.HydroError) as e:
+            H.hydro_cfl_dt_boxes(None, 0.45, ws, precision=prec, _carray=arr)
+        assert e.value.code == H.EINVAL
