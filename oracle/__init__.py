@@ -89,6 +89,8 @@ def lib():
         L.orc_recon1d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, _dp, _dp]
         L.orc_recon_line.argtypes = [ctypes.POINTER(_OrcParams), ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
         L.orc_trace.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, ctypes.c_double, _dp, _dp]
+        L.orc_split_row.argtypes = [ctypes.POINTER(_OrcParams), _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, _dp, _dp]
         L.orc_riemann.restype = ctypes.c_uint
         L.orc_riemann.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, _dp, _dp, _dp]
@@ -188,6 +190,19 @@ def recon1d(recon, limiter_kind, w, theta=1.0):
     wR = np.full(n, np.nan)
     lib().orc_recon1d(recon, limiter_kind, theta, _ptr(w), n, _ptr(wL), _ptr(wR))
     return wL, wR
+
+
+def split_row(params: Params, u, lo, hi, dx):
+    """One RTVD / WAF sweep (params.scheme) of a row of conserved states
+    u [n][5] in the sweep's local frame (normal momentum second) with the
+    full params.dt: returns (the row updated on [lo, hi), flux through face
+    lo - 1/2, flux through face hi - 1/2)."""
+    u = np.array(u, dtype=np.float64, order="C")
+    n = u.shape[0]
+    assert u.shape == (n, 5)
+    Flo, Fhi = np.zeros(5), np.zeros(5)
+    lib().orc_split_row(ctypes.byref(params.c()), _ptr(u), n, int(lo), int(hi), float(dx), _ptr(Flo), _ptr(Fhi))
+    return u, Flo, Fhi
 
 
 def trace(recon, W0, a, b, dtdx, gamma=1.4):

@@ -175,6 +175,24 @@ void orc_recon1d(int recon, int limiter, double theta, const double* w, int n, d
   }
 }
 
+// One sweep of a split scheme (RTVD or WAF per p->scheme) along one row of n
+// conserved states u [n][5] in the local frame of the sweep (normal momentum
+// second), updated in place on the cells [lo, hi) with the full dt over dx;
+// Flo / Fhi receive the fluxes through the faces lo - 1/2 and hi - 1/2.
+void orc_split_row(const OrcParams* p, double* u, int n, int lo, int hi, double dx, double* Flo, double* Fhi) {
+  Params<double> P = to_params(p);
+  std::vector<std::array<double, 5>> row(n);
+  for (int j = 0; j < n; ++j)
+    for (int v = 0; v < 5; ++v) row[j][v] = u[j * 5 + v];
+  const double dtdx = P.dt / dx, hdtdx = 0.5 * P.dt / dx;
+  if (P.scheme == SCH_RTVD)
+    rtvd_row(P, row, lo, hi, dtdx, hdtdx, Flo, Fhi);
+  else
+    waf_row(P, row, lo, hi, dtdx, Flo, Fhi);
+  for (int j = 0; j < n; ++j)
+    for (int v = 0; v < 5; ++v) u[j * 5 + v] = row[j][v];
+}
+
 // Characteristic tracing of one cell (local frame arrays).  For PLM, a = slope
 // and b is ignored; for PPM, a / b are the left / right face values.
 void orc_trace(int recon, double gamma, const double* W0, const double* a, const double* b, double dtdx,
