@@ -164,3 +164,38 @@ def test_readme_c_example_compiles_against_the_header(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I" + os.path.join(ROOT, "include"),
                         str(f)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_cfl_box_interior_description_is_checked_on_the_host():
+    """hydro_cfl_dt_boxes refuses a malformed description of halo-padded
+    groups (ghost > 0) before any device work, and lets a well-formed one
+    through to its workspace check (the pointers are never dereferenced on
+    these paths)."""
+    from paper_1103_3373_gb300 import hydro as H
+    lib = H._lib()
+    lib.hydro_cfl_dt_boxes.restype = ctypes.c_int
+    n, g = 16, 3
+    M = n + 2 * g
+
+    def box(**kw):
+        arr = (H._CCflBox * 1)()
+        e = arr[0]
+        e.U, e.dt_dev = 16, 32
+        e.G, e.group_stride, e.var_stride, e.cells = 4, 5 * M ** 3, M ** 3, n ** 3
+        for d in range(3):
+            e.dx[d] = 0.1
+        e.dt_scale, e.interior_n, e.ghost = 1.0, n, g
+        for k, v in kw.items():
+            setattr(e, k, v)
+        return arr
+
+    def call(arr, ws=None, nbytes=0):
+        return lib.hydro_cfl_dt_boxes(arr, 1, H.FP32, ctypes.c_double(1.4), ctypes.c_double(0.0),
+                                      ctypes.c_double(0.0), ctypes.c_double(0.4), None, ws, ctypes.c_size_t(nbytes),
+                                      None)
+
+    for kw in (dict(ghost=-1), dict(interior_n=0), dict(cells=n ** 3 - 1), dict(var_stride=M ** 3 - 1),
+               dict(cells=M ** 3)):
+        assert call(box(**kw)) == H.EINVAL, kw
+    assert call(box()) == H.EWORKSPACE
+    assert call(box(ghost=0, cells=M ** 3, interior_n=0)) == H.EWORKSPACE  # contiguous cells
