@@ -354,7 +354,8 @@ cudaError_t launch_prepare(const LevelView& F, const LevelView& C, const S* cnew
 }
 
 // Coarse-grid correction: CTA q handles coarse group q of C (corrected in
-// place in Uc); faces -x,+x,-y,+y,-z,+z in order per cell.
+// place in Uc); faces -x,+x,-y,+y,-z,+z in order per cell, one face of the
+// group at a time.
 template <class S>
 __global__ void __launch_bounds__(AMR_THREADS)
     amr_reflux_kernel(LevelView C, S* __restrict__ Uc, const S* __restrict__ cflux, LevelView F,
@@ -395,17 +396,24 @@ __global__ void __launch_bounds__(AMR_THREADS)
     __syncthreads();
     const bool any = on[0] || on[1] || on[2] || on[3] || on[4] || on[5];
     if (any) {
-      for (int cell = threadIdx.x; cell < (int)N3; cell += blockDim.x) {
-        const int l[3] = {cell % AN, (cell / AN) % AN, cell / NN};
-        S u[5];
-        bool loaded = false;
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-          if (!on[f]) continue;
-          const int d = f >> 1, side = f & 1;
-          if (l[d] != (side ? AN - 1 : 0)) continue;
-          const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-          const int a = l[t2], b = l[t1];
+      // one face at a time, -x,+x,-y,+y,-z,+z, its N^2 cells spread over the
+      // CTA: a cell on an edge or a corner takes its faces' corrections in
+      // that order, each read back from memory (same rounding as applying
+      // them one after another in registers)
+      for (int f = 0; f < 6; ++f) {
+        if (!on[f]) continue;  // uniform across the CTA
+        const int d = f >> 1, side = f & 1;
+        const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        const int ffc = 2 * d + (side ? 0 : 1);
+        const S sg = side ? S(-1) : S(1);
+        const S h = d == 0 ? h0 : (d == 1 ? h1 : h2);
+        for (int ab = threadIdx.x; ab < NN; ab += blockDim.x) {
+          const int a = ab / AN, b = ab - a * AN;  // along t2, along t1
+          int l[3];
+          l[d] = side ? AN - 1 : 0;
+          l[t2] = a;
+          l[t1] = b;
+          const long long cell = ((long long)l[2] * AN + l[1]) * AN + l[0];
           // fine cells across the face and their face toward this cell
           int fc[3];
           fc[d] = 2 * nbs[f] * AN + (side ? 0 : 2 * AN - 1);
@@ -416,14 +424,8 @@ __global__ void __launch_bounds__(AMR_THREADS)
             raise_err(err, HYDRO_AMR_EOCTET);
             continue;
           }
-          const int ffc = 2 * d + (side ? 0 : 1);
           const int a0 = fc[t2] % AN, b0 = fc[t1] % AN;
-          if (!loaded) {
-#pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = Uc[(long long)q * 5 * N3 + v * N3 + cell];
-            loaded = true;
-          }
-          const S sg = side ? S(-1) : S(1);
+          S* uc = Uc + (long long)q * 5 * N3 + cell;
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             const S Fc = cflux[(((long long)q * 6 + f) * 5 + v) * NN + a * AN + b];
@@ -437,13 +439,10 @@ __global__ void __launch_bounds__(AMR_THREADS)
             s1 = s1 + p1[(a0 + 1) * AN + b0];
             s1 = s1 + p1[(a0 + 1) * AN + b0 + 1];
             const S Fbar = S(0.125) * (s0 + s1);
-            u[v] = u[v] + sg * ((d == 0 ? h0 : (d == 1 ? h1 : h2)) * (Fbar - Fc));
+            uc[v * N3] = uc[v * N3] + sg * (h * (Fbar - Fc));
           }
         }
-        if (loaded) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) Uc[(long long)q * 5 * N3 + v * N3 + cell] = u[v];
-        }
+        __syncthreads();
       }
     }
     __syncthreads();
